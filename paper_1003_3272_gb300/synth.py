@@ -1,0 +1,255 @@
+"""Seeded synthetic inputs for the NMF workloads.
+
+This module is the one piece of code shared by the CUDA path, the FP64 oracle,
+the tests and the benchmark: it only *draws numbers*.  It contains none of the
+multiplicative-update arithmetic.
+
+Generator: a counter-based SplitMix64 (Steele, Lea & Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014).  Word ``i`` of stream ``s`` under
+seed ``seed`` is
+
+    key  = mix64(seed + (s + 1) * GAMMA)          (mod 2**64)
+    word = mix64(key  + (i + 1) * GAMMA)          (mod 2**64)
+
+with GAMMA = 0x9E3779B97F4A7C15 and the SplitMix64 finaliser
+
+    mix64(z): z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9
+              z = (z ^ (z >> 27)) * 0x94D049BB133111EB
+              return z ^ (z >> 31)
+
+Distributions (all produced in float32 unless stated):
+  * uniform on [0,1):   (word >> 40) * 2**-24                 exact in fp32
+  * uniform on (0,1):   ((word >> 40) + 0.5) * 2**-24         exact, never 0 or 1
+  * Exponential(1) = Gamma(1,1):  -log(((word >> 11) + 0.5) * 2**-53) in fp64,
+    rounded once to fp32
+  * |N(0, sigma^2)|:  Box-Muller on words 2i (radius) and 2i+1 (angle), fp64,
+    rounded once to fp32
+
+The CUDA library's seeded initialisation of W and H (Algorithm 1's "draw
+uniform on (0,1)") implements the same uniform-(0,1) definition on the device;
+a test checks the two bit for bit.
+
+Workloads: the five problem families the method is measured on (a CBCL-shaped
+faces matrix, a planted low-rank matrix, a tall uniform matrix for the
+precision sweep, a batch of small uneven problems and a large streaming
+matrix).  Each builder returns V together with the seeded starting factors.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+# Stream ids: the data matrix, the left and right starting factors, and the
+# planted factors / noise of the planted workload.
+STREAM_V = 0
+STREAM_W = 1
+STREAM_H = 2
+STREAM_WSTAR = 3
+STREAM_HSTAR = 4
+STREAM_NOISE = 5
+STREAM_SHAPES = 6
+
+BASE_SEED = 20100316
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    z = z.astype(np.uint64, copy=True)
+    z ^= z >> np.uint64(30)
+    z *= _M1
+    z ^= z >> np.uint64(27)
+    z *= _M2
+    z ^= z >> np.uint64(31)
+    return z
+
+
+def stream_key(seed: int, stream: int) -> np.uint64:
+    with np.errstate(over="ignore"):
+        z = np.array([seed % (1 << 64)], dtype=np.uint64)
+        z = z + np.uint64(stream + 1) * GAMMA
+        return _mix64(z)[0]
+
+
+def words(seed: int, stream: int, start: int, count: int) -> np.ndarray:
+    """Raw 64-bit words ``start .. start+count-1`` of one stream."""
+    key = stream_key(seed, stream)
+    with np.errstate(over="ignore"):
+        idx = np.arange(start + 1, start + count + 1, dtype=np.uint64)
+        return _mix64(key + idx * GAMMA)
+
+
+_CHUNK = 1 << 22
+
+
+def _fill(seed, stream, count, fn, dtype=np.float32):
+    out = np.empty(count, dtype=dtype)
+    for s in range(0, count, _CHUNK):
+        c = min(_CHUNK, count - s)
+        out[s:s + c] = fn(words(seed, stream, s, c))
+    return out
+
+
+def uniform_open(seed: int, stream: int, shape) -> np.ndarray:
+    """iid uniform on (0,1), float32, row-major ``shape``."""
+    n = int(np.prod(shape))
+    f = lambda w: ((w >> np.uint64(40)).astype(np.float64) + 0.5) * 2.0 ** -24
+    return _fill(seed, stream, n, f).reshape(shape)
+
+
+def uniform_closed_open(seed: int, stream: int, shape) -> np.ndarray:
+    """iid uniform on [0,1), float32."""
+    n = int(np.prod(shape))
+    f = lambda w: (w >> np.uint64(40)).astype(np.float64) * 2.0 ** -24
+    return _fill(seed, stream, n, f).reshape(shape)
+
+
+def exponential(seed: int, stream: int, shape) -> np.ndarray:
+    """iid Exponential(1) (= Gamma(1,1)), float32."""
+    n = int(np.prod(shape))
+    f = lambda w: -np.log(((w >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53)
+    return _fill(seed, stream, n, f).reshape(shape)
+
+
+def abs_normal(seed: int, stream: int, shape, sigma: float) -> np.ndarray:
+    """iid |N(0, sigma^2)|, float32 (Box-Muller over word pairs)."""
+    n = int(np.prod(shape))
+    out = np.empty(n, dtype=np.float32)
+    for s in range(0, n, _CHUNK):
+        c = min(_CHUNK, n - s)
+        w = words(seed, stream, 2 * s, 2 * c)
+        u1 = ((w[0::2] >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
+        u2 = ((w[1::2] >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
+        z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+        out[s:s + c] = np.abs(sigma * z)
+    return out.reshape(shape)
+
+
+def uniform_int(seed: int, stream: int, count: int, lo: int, hi: int) -> np.ndarray:
+    """iid integers uniform on {lo..hi} (inclusive), by the widening multiply
+    of the top 32 bits (Lemire's method without the rejection step; the bias
+    is below 2**-20 for the ranges used here)."""
+    w = words(seed, stream, 0, count) >> np.uint64(32)
+    span = np.uint64(hi - lo + 1)
+    return (lo + ((w * span) >> np.uint64(32)).astype(np.int64)).astype(np.int64)
+
+
+# ----------------------------------------------------------------------------
+# Workloads
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Problem:
+    """One NMF problem: V (p x n) ~= W (p x r) @ H (r x n)."""
+    name: str
+    V: np.ndarray           # float32 (p, n), row-major
+    W0: np.ndarray          # float32 (p, r)
+    H0: np.ndarray          # float32 (r, n)
+    r: int
+    iters: int
+    eps: float = 1e-10
+    seed: int = BASE_SEED
+
+    @property
+    def p(self):
+        return self.V.shape[0]
+
+    @property
+    def n(self):
+        return self.V.shape[1]
+
+
+def starting_factors(seed: int, p: int, n: int, r: int):
+    """Algorithm 1's start: W and H iid uniform on (0,1)."""
+    return (uniform_open(seed, STREAM_W, (p, r)),
+            uniform_open(seed, STREAM_H, (r, n)))
+
+
+def uniform_problem(p: int, n: int, r: int, seed: int, iters: int = 10,
+                    name: str = "uniform", eps: float = 1e-10) -> Problem:
+    """V iid uniform on [0,1) (the faces-shaped and tall sweep workloads)."""
+    V = uniform_closed_open(seed, STREAM_V, (p, n))
+    W0, H0 = starting_factors(seed, p, n, r)
+    return Problem(name, V, W0, H0, r, iters, eps, seed)
+
+
+def exponential_problem(p: int, n: int, r: int, seed: int, iters: int = 20,
+                        name: str = "exponential", eps: float = 1e-10) -> Problem:
+    """V iid Exponential(1) (the large streaming workload)."""
+    V = exponential(seed, STREAM_V, (p, n))
+    W0, H0 = starting_factors(seed, p, n, r)
+    return Problem(name, V, W0, H0, r, iters, eps, seed)
+
+
+def planted_problem(p: int, n: int, r: int, seed: int, sigma: float = 0.01,
+                    iters: int = 200, name: str = "planted",
+                    eps: float = 1e-10) -> Problem:
+    """V = W* H* + |N(0, sigma^2)| with W*, H* iid Gamma(1,1).
+
+    The planted product is formed in float64 and rounded once to float32
+    together with the noise."""
+    Ws = exponential(seed, STREAM_WSTAR, (p, r)).astype(np.float64)
+    Hs = exponential(seed, STREAM_HSTAR, (r, n)).astype(np.float64)
+    E = abs_normal(seed, STREAM_NOISE, (p, n), sigma).astype(np.float64)
+    V = (Ws @ Hs + E).astype(np.float32)
+    W0, H0 = starting_factors(seed, p, n, r)
+    return Problem(name, V, W0, H0, r, iters, eps, seed)
+
+
+def exact_planted(p: int, n: int, r: int, seed: int) -> Problem:
+    """V = W0 H0 exactly representable: W0 and H0 hold small integers on a
+    power-of-two grid so that every product and partial sum is exact in
+    float32; the starting factors *are* the planted factors (a fixed point
+    of the multiplicative updates when eps = 0)."""
+    w = words(seed, STREAM_WSTAR, 0, p * r)
+    h = words(seed, STREAM_HSTAR, 0, r * n)
+    W0 = ((w >> np.uint64(61)).astype(np.float32) + 1.0).reshape(p, r) / 8.0
+    H0 = ((h >> np.uint64(61)).astype(np.float32) + 1.0).reshape(r, n) / 4.0
+    V = (W0.astype(np.float64) @ H0.astype(np.float64)).astype(np.float32)
+    return Problem("exact_planted", V, W0.astype(np.float32), H0.astype(np.float32),
+                   r, 10, 0.0, seed)
+
+
+# The five measured configurations, by what they are.
+FACES = dict(name="faces_361x2429_r10", p=361, n=2429, r=10, iters=50)
+PLANTED = dict(name="planted_8192x8192_r50", p=8192, n=8192, r=50, iters=200)
+TALL = dict(name="tall_65536x4096", p=65536, n=4096, iters=20)
+LARGE = dict(name="large_131072x16384_r64", p=131072, n=16384, r=64, iters=20)
+BATCH = dict(name="batched_512", count=512, pmin=64, pmax=2048, rmin=4, rmax=32,
+             iters=100)
+
+
+def faces(seed: int = BASE_SEED + 0) -> Problem:
+    c = FACES
+    return uniform_problem(c["p"], c["n"], c["r"], seed, c["iters"], c["name"])
+
+
+def planted(seed: int = BASE_SEED + 1, p: int = 8192, n: int = 8192,
+            r: int = 50, iters: int = 200) -> Problem:
+    return planted_problem(p, n, r, seed, 0.01, iters,
+                           f"planted_{p}x{n}_r{r}")
+
+
+def batch_shapes(count: int = 512, seed: int = BASE_SEED + 3,
+                 pmin: int = 64, pmax: int = 2048, rmin: int = 4, rmax: int = 32):
+    """Per-instance (p, n, r) of the batched workload: p, n iid uniform on
+    {pmin..pmax}, r iid uniform on {rmin..rmax}."""
+    ps = uniform_int(seed, STREAM_SHAPES, count, pmin, pmax)
+    ns = uniform_int(seed + 1, STREAM_SHAPES, count, pmin, pmax)
+    rs = uniform_int(seed + 2, STREAM_SHAPES, count, rmin, rmax)
+    return [(int(a), int(b), int(c)) for a, b, c in zip(ps, ns, rs)]
+
+
+def batch(count: int = 512, seed: int = BASE_SEED + 3, iters: int = 100,
+          pmin: int = 64, pmax: int = 2048, rmin: int = 4, rmax: int = 32):
+    """The batched workload: independent problems with V iid uniform on [0,1);
+    instance ``b`` uses seed ``seed * 1000 + b``."""
+    probs = []
+    for b, (p, n, r) in enumerate(batch_shapes(count, seed, pmin, pmax, rmin, rmax)):
+        probs.append(uniform_problem(p, n, r, seed * 1000 + b, iters,
+                                     f"batch{b}_{p}x{n}_r{r}"))
+    return probs
