@@ -1,0 +1,188 @@
+/*
+ * nmf.h -- C ABI of the GB300 multiplicative-update NMF library (libnmf.so).
+ *
+ * The method: Zhou, Lange & Suchard, "Graphics Processing Units and
+ * High-Dimensional Optimization", Section 3.1.  Given a nonnegative data
+ * matrix V (p x n), find nonnegative W (p x r) and H (r x n) minimising the
+ * Frobenius objective f = ||V - W H||_F^2 (Eq. (3.1); Algorithm 1 states the
+ * problem).  The paper's letters X, V, W are this library's V, W, H.
+ *
+ * One iteration (Algorithm 1's loop body; Eqs. (3.3) and (3.4)), with eps
+ * added to the denominators only:
+ *     H <- H .* (W^T V) ./ ((W^T W) H + eps)       right-factor update
+ *     W <- W .* (V H^T) ./ (W (H H^T) + eps)       left-factor update
+ * Default order: H first, then W (NMF_ORDER_H_FIRST).  NMF_ORDER_W_FIRST
+ * is Algorithm 1's own order.  Both are MM block-relaxation steps with the
+ * descent property (Section 2, Eq. (3.2)).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are float32, row-major, densely packed (leading dimension =
+ *     number of columns): V is p x n, W is p x r, H is r x n.
+ *   - Pointers marked "device" must be CUDA device (or managed) memory of
+ *     the current device; "host" means ordinary or pinned host memory.
+ *   - The caller owns V, W and H.  V must stay alive and unchanged for the
+ *     life of a context; W and H are read and updated in place.
+ *   - The library owns its workspaces (operand copies of V in the layout and
+ *     precision of the chosen arithmetic, split-K partial sums, Gram
+ *     matrices, objective partials) and frees them in nmf_destroy.
+ *   - Errors are reported only through the return code (never by exception,
+ *     abort or device trap).  nmf_last_error() gives a one-line reason.
+ *   - A context is bound to one CUDA stream and is not thread-safe; use one
+ *     context per stream.  Asynchronous calls enqueue work on that stream.
+ *   - Results are deterministic: no floating-point atomics; every reduction
+ *     runs in a fixed order, so repeated runs are bitwise identical.
+ */
+#ifndef NMF_H_
+#define NMF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NMF_OK = 0,
+  NMF_EINVAL = 1,        /* bad argument: null pointer, size, rank, eps, enum  */
+  NMF_ENOMEM = 2,        /* device or host allocation failed                   */
+  NMF_ECUDA = 3,         /* a CUDA runtime/driver call or launch failed        */
+  NMF_ETIMEOUT = 4,      /* a bounded device-side wait ran out (no hang)       */
+  NMF_ENONFINITE = 5,    /* V holds a negative, NaN or infinite entry          */
+  NMF_EUNSUPPORTED = 6   /* valid request this build or device cannot serve    */
+} nmf_status;
+
+/* Arithmetic of the two V-streaming products W^T V and V H^T.  All forms
+ * accumulate in float32; the element-wise update, the Gram matrices and the
+ * objective are float32/float64 in every form.
+ *   NMF_FP32   : float32 FMA on the SM cores (the plain reference form)
+ *   NMF_TF32   : tcgen05 tensor cores, TF32 operands
+ *   NMF_BF16X3 : tcgen05, each operand split x = hi + lo (both bf16);
+ *                products hi*hi + hi*lo + lo*hi
+ *   NMF_BF16   : tcgen05, operands rounded to bf16 (half the bytes of V)    */
+typedef enum {
+  NMF_FP32 = 0,
+  NMF_TF32 = 1,
+  NMF_BF16X3 = 2,
+  NMF_BF16 = 3
+} nmf_precision;
+
+typedef enum {
+  NMF_ORDER_H_FIRST = 0, /* H then W                                        */
+  NMF_ORDER_W_FIRST = 1  /* W then H: Algorithm 1's order                   */
+} nmf_order;
+
+typedef struct {
+  int64_t p;             /* rows of V and W                                 */
+  int64_t n;             /* columns of V and H                              */
+  int32_t r;             /* rank: 1 <= r <= 128, r <= min(p, n)             */
+  float eps;             /* >= 0, added to every update denominator         */
+  nmf_precision prec;
+  nmf_order order;
+  uint64_t seed;         /* used when init_from_seed != 0                   */
+  int32_t init_from_seed;/* 1: nmf_init overwrites W, H with iid uniform(0,1)
+                            draws (Algorithm 1's start; counter-based
+                            SplitMix64, W on stream 1, H on stream 2)        */
+  int32_t validate;      /* 1: nmf_init rejects V with a negative or
+                            non-finite entry (NMF_ENONFINITE)               */
+  int32_t split_k;       /* 0: automatic; otherwise the number of K-splits
+                            per output tile of each product (tuning knob)   */
+  int32_t reserved;
+} nmf_config;
+
+typedef struct nmf_ctx nmf_ctx;
+typedef struct nmf_batch nmf_batch;
+
+/* Fill *cfg with defaults for a p x n problem of rank r: eps = 1e-10,
+ * NMF_FP32, NMF_ORDER_H_FIRST, seed 0, no seeded init, no validation,
+ * automatic split.  Returns NMF_EINVAL if cfg is null.                      */
+nmf_status nmf_config_default(nmf_config* cfg, int64_t p, int64_t n, int32_t r);
+
+/* Create a context for V (device, p x n), W (device, p x r), H (device,
+ * r x n) on `stream` (a cudaStream_t; NULL = legacy default stream).
+ * Allocates the workspaces, builds V's operand copies for the chosen
+ * precision (one pass over V), optionally seeds W and H, and forms the Gram
+ * matrices W^T W and H H^T of the starting factors.  Asynchronous on the
+ * stream except for allocation.  On failure *out is NULL and nothing is
+ * leaked.                                                                    */
+nmf_status nmf_init(const nmf_config* cfg, const float* V, float* W, float* H,
+                    void* stream, nmf_ctx** out);
+
+/* Run `iters` >= 0 MM iterations (Algorithm 1's loop body, in cfg.order),
+ * updating W and H in place.  Asynchronous on the context's stream.       */
+nmf_status nmf_step(nmf_ctx* ctx, int iters);
+
+/* One block update only: which = 0 updates H (Eq. (3.4) in the paper's
+ * letters), which = 1 updates W (Eq. (3.3)).  nmf_step(ctx, 1) equals the
+ * two half steps in cfg.order.  Asynchronous.                               */
+nmf_status nmf_half_step(nmf_ctx* ctx, int which);
+
+/* f = ||V - W H||_F^2 (Eq. (3.1)) at the current W, H, as a direct residual
+ * summed in float64 in a fixed order; *f_out is host memory.  Synchronises
+ * the stream.                                                               */
+nmf_status nmf_objective(nmf_ctx* ctx, double* f_out);
+
+/* Algorithm 1 with Section 3's stopping rule: iterate until
+ * |f_k - f_{k-1}| / (|f_{k-1}| + 1) < tol or max_iters iterations, testing
+ * the objective every `check_every` >= 1 iterations.  *iters_done and *f_out
+ * (host) receive the count and the last objective.  Synchronises.          */
+nmf_status nmf_run(nmf_ctx* ctx, int max_iters, double tol, int check_every,
+                   int* iters_done, double* f_out);
+
+/* Restart from Algorithm 1's seeded start on the same V (multiple random
+ * starts): rebuild V's operand copies (one pass over V), draw W and H iid
+ * uniform(0,1) from `seed` exactly as init_from_seed does, and re-form the
+ * Gram matrices.  No allocation.  Asynchronous.                            */
+nmf_status nmf_restart(nmf_ctx* ctx, uint64_t seed);
+
+/* Copy the current Gram matrix (which = 0: W^T W, which = 1: H H^T) into
+ * host memory `out` (r*r doubles, row-major).  Synchronises.              */
+nmf_status nmf_read_gram(nmf_ctx* ctx, int which, double* out);
+
+/* One-call solve: V, W, H may each be host or device pointers (detected per
+ * pointer).  Host inputs are copied in, `iters` iterations run, W and H are
+ * copied back to host outputs and, if f_out is not NULL, the final objective
+ * is written there (host).  Synchronises; uses `stream` for all work.      */
+nmf_status nmf_solve(const nmf_config* cfg, const float* V, float* W, float* H,
+                     int iters, double* f_out, void* stream);
+
+void nmf_destroy(nmf_ctx* ctx);
+
+/* ---- Batched form: many independent problems in one grouped launch -------
+ * Instance b has its own cfgs[b] (p, n, r, eps; precision must be the same
+ * for all, order is H first), V[b] (device), W[b], H[b] (device, updated in
+ * place).  Every iteration of every instance runs inside one persistent
+ * grouped kernel per iteration, replayed from a CUDA graph.  The pointer
+ * arrays are host memory and are copied at init.                            */
+nmf_status nmf_batched_init(int count, const nmf_config* cfgs,
+                            const float* const* V, float* const* W,
+                            float* const* H, void* stream, nmf_batch** out);
+nmf_status nmf_batched_step(nmf_batch* b, int iters);
+/* f_out: host array of `count` doubles.  Synchronises.                    */
+nmf_status nmf_batched_objective(nmf_batch* b, double* f_out);
+void nmf_batched_destroy(nmf_batch* b);
+
+/* ---- Instrumentation ---------------------------------------------------
+ * Number of kernels this library has launched in this process (all
+ * contexts), for launch accounting.                                         */
+uint64_t nmf_kernel_launches(void);
+/* Enable (on != 0) or disable CUDA-event timing of the context's kernels by
+ * kind; enabling clears the totals.  Kinds: 0 = the V-streaming products
+ * with their fused epilogues, 1 = Gram reductions, 2 = objective,
+ * 3 = operand copies / seeding / starting Grams.                           */
+nmf_status nmf_profile_enable(nmf_ctx* ctx, int on);
+/* Total milliseconds and launch count recorded for `kind` since enabling.
+ * Synchronises the stream.                                                 */
+nmf_status nmf_profile_read(nmf_ctx* ctx, int kind, double* ms, int64_t* count);
+
+const char* nmf_status_str(nmf_status s);
+/* Reason for the last failure on ctx (or, with ctx == NULL, the last failure
+ * of any call on this thread).  Never NULL.                                */
+const char* nmf_last_error(const nmf_ctx* ctx);
+/* Library version string.                                                  */
+const char* nmf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NMF_H_ */

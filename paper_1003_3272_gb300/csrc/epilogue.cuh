@@ -1,0 +1,137 @@
+// Fused multiply-divide epilogue of one MM half step (Section 3.1,
+// Eqs. (3.3)-(3.4)), run by the block that owns a finished output tile.
+//
+// Tile space: rows m of the tile are rows of W (left update, p rows) or
+// columns of H (right update, n columns); columns k are the r factor ranks.
+// In both cases the update of entry (m, k) is
+//     new[m,k] = old[m,k] * num[m,k] / (sum_l old[m,l] G[l,k] + eps)
+// where num is the V-streaming product (V H^T or (W^T V)^T) and G the r x r
+// Gram matrix of the *other* factor (H H^T or W^T W).  The denominator is
+// the paper's V_n W_n W_n^t (resp. V^t V W_n) grouped through the Gram
+// matrix.  Multiplication and division are IEEE round-to-nearest (no fast
+// math), matching (old * num) / den.
+//
+// The block then writes the new factor (user storage and the operand
+// plane(s) the next product streams) and the tile's partial Gram matrix
+// sum_m new[m,:]^T new[m,:], summed over m in a fixed order.
+#pragma once
+
+#include "nmf_internal.cuh"
+
+namespace nmf {
+
+// Shared-memory floats needed by mu_epilogue for a BM x RPAD tile.
+template <int BM, int RPAD>
+constexpr int epi_smem_floats() {
+  return 2 * BM * (RPAD + 1) + RPAD * RPAD;
+}
+
+__device__ __forceinline__ void store_plane(const EpiArgs& e, int k, int64_t m, float v) {
+  const int64_t off = (int64_t)k * e.ldop + m;
+  if (e.plane == kPlaneF32) {
+    static_cast<float*>(e.op_hi)[off] = v;
+  } else if (e.plane == kPlaneTF32) {
+    static_cast<float*>(e.op_hi)[off] = round_tf32(v);
+  } else {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    static_cast<__nv_bfloat16*>(e.op_hi)[off] = hi;
+    if (e.plane == kPlaneBF16x2) {
+      const float rem = __fsub_rn(v, __bfloat162float(hi));
+      static_cast<__nv_bfloat16*>(e.op_lo)[off] = __float2bfloat16_rn(rem);
+    }
+  }
+}
+
+// Ns: [BM][RPAD+1] holds the final numerator tile on entry (rows >= M - m0
+//     are ignored) and the new factor tile on exit.
+// Os: [BM][RPAD+1] scratch for the old factor tile.
+// Gs: [RPAD][RPAD] scratch for the Gram matrix.
+// All NT threads of the block must call it.
+template <int BM, int RPAD, int NT>
+__device__ void mu_epilogue(float* Ns, float* Os, float* Gs, int64_t m0, int tile,
+                            const EpiArgs& e) {
+  constexpr int LD = RPAD + 1;
+  const int tid = threadIdx.x;
+  const int r = e.r;
+  const int64_t M = e.M;
+  const int rows = (int)((M - m0) < BM ? (M - m0) : BM);
+
+  for (int i = tid; i < RPAD * RPAD; i += NT) {
+    const int l = i / RPAD, k = i % RPAD;
+    Gs[i] = (l < r && k < r) ? e.G[l * r + k] : 0.f;
+  }
+  if (e.layout == kFactorRowMajor) {
+    for (int i = tid; i < BM * RPAD; i += NT) {
+      const int m = i / RPAD, k = i % RPAD;
+      Os[m * LD + k] = (m < rows && k < r) ? e.F[(m0 + m) * r + k] : 0.f;
+    }
+  } else {
+    for (int i = tid; i < BM * RPAD; i += NT) {
+      const int k = i / BM, m = i % BM;
+      Os[m * LD + k] = (m < rows && k < r) ? e.F[(int64_t)k * e.ldf + m0 + m] : 0.f;
+    }
+  }
+  __syncthreads();
+
+  // new = old * num / (old . G[:, k] + eps), eight ranks per work item.
+  constexpr int KG = RPAD / 8;
+  for (int it = tid; it < BM * KG; it += NT) {
+    const int m = it % BM, kg = it / BM;
+    float den[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) den[j] = 0.f;
+    for (int l = 0; l < r; ++l) {
+      const float o = Os[m * LD + l];
+      const float4 g0 = *reinterpret_cast<const float4*>(&Gs[l * RPAD + kg * 8]);
+      const float4 g1 = *reinterpret_cast<const float4*>(&Gs[l * RPAD + kg * 8 + 4]);
+      den[0] = fmaf(o, g0.x, den[0]); den[1] = fmaf(o, g0.y, den[1]);
+      den[2] = fmaf(o, g0.z, den[2]); den[3] = fmaf(o, g0.w, den[3]);
+      den[4] = fmaf(o, g1.x, den[4]); den[5] = fmaf(o, g1.y, den[5]);
+      den[6] = fmaf(o, g1.z, den[6]); den[7] = fmaf(o, g1.w, den[7]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = kg * 8 + j;
+      float v = 0.f;
+      if (m < rows && k < r) {
+        const float d = __fadd_rn(den[j], e.eps);
+        v = __fdiv_rn(__fmul_rn(Os[m * LD + k], Ns[m * LD + k]), d);
+      }
+      Ns[m * LD + k] = v;
+    }
+  }
+  __syncthreads();
+
+  // Write the new factor and its operand plane(s).
+  if (e.layout == kFactorRowMajor) {
+    for (int i = tid; i < rows * r; i += NT) {
+      const int m = i / r, k = i % r;
+      e.F[(m0 + m) * r + k] = Ns[m * LD + k];
+    }
+  } else {
+    for (int i = tid; i < rows * r; i += NT) {
+      const int k = i / rows, m = i % rows;
+      e.F[(int64_t)k * e.ldf + m0 + m] = Ns[m * LD + k];
+    }
+  }
+  for (int i = tid; i < rows * r; i += NT) {
+    const int k = i / rows, m = i % rows;
+    store_plane(e, k, m0 + m, Ns[m * LD + k]);
+  }
+
+  // Partial Gram of the new tile: P[k][l] = sum_m new[m,k] new[m,l], k <= l.
+  float* P = e.gram_part + (int64_t)tile * r * r;
+  const int npairs = r * (r + 1) / 2;
+  for (int it = tid; it < npairs; it += NT) {
+    // unrank (k, l) with k <= l
+    int k = 0, rem = it;
+    while (rem >= r - k) { rem -= r - k; ++k; }
+    const int l = k + rem;
+    float s = 0.f;
+    for (int m = 0; m < rows; ++m) s = fmaf(Ns[m * LD + k], Ns[m * LD + l], s);
+    P[k * r + l] = s;
+    P[l * r + k] = s;
+  }
+}
+
+}  // namespace nmf

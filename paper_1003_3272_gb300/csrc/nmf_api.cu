@@ -1,0 +1,645 @@
+// C ABI of the MM NMF library: contexts, workspaces, validation and the
+// per-iteration launch sequence.  See include/nmf.h for the contract.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "nmf_internal.cuh"
+#include "tc.cuh"
+
+using namespace nmf;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+std::atomic<uint64_t> g_launches{0};
+
+inline void launched(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+
+void set_err(std::string* dst, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  if (dst) *dst = buf;
+}
+
+}  // namespace
+
+// One V-streaming product followed by its fused epilogue: which operands,
+// which factor, which workspace.
+struct HalfPlan {
+  // X operand (M x K, K contiguous) in the precision's format
+  const void* X_hi = nullptr;
+  const void* X_lo = nullptr;
+  int64_t ldx = 0;
+  // Y operand: plane of the other factor (r x K)
+  const void* Y_hi = nullptr;
+  const void* Y_lo = nullptr;
+  int64_t ldy = 0;
+  int64_t M = 0, K = 0;
+  int splits = 1;
+  int64_t kchunk = 0;
+  int tiles = 0;
+  EpiArgs ep{};
+  float* G32_out = nullptr;   // Gram of the updated factor (output of the reduce)
+  double* G64_out = nullptr;
+  TcPlan tc{};                // tcgen05 launch plan (tensor-core precisions)
+};
+
+struct nmf_ctx {
+  nmf_config cfg{};
+  const float* V = nullptr;
+  float* W = nullptr;
+  float* H = nullptr;
+  cudaStream_t st = nullptr;
+  int64_t p = 0, n = 0;
+  int r = 0;
+  int sms = 0;
+  std::string err = "no error";
+  std::vector<void*> allocs;
+
+  // operand copies of V: Xw (p x ld_n) streams the left update, Xh (n x ld_p)
+  // the right update; *_hi / *_lo for the bf16 forms, f32 otherwise.
+  const void* Xw_hi = nullptr; const void* Xw_lo = nullptr;
+  const void* Xh_hi = nullptr; const void* Xh_lo = nullptr;
+  int64_t ld_n = 0, ld_p = 0;
+  // factor planes: Wop = W^T (r x ld_p), Hop = H (r x ld_n)
+  void* Wop_hi = nullptr; void* Wop_lo = nullptr;
+  void* Hop_hi = nullptr; void* Hop_lo = nullptr;
+  int plane = kPlaneF32;
+  int rpad = 0;
+  // Grams
+  float* GW32 = nullptr; double* GW64 = nullptr;
+  float* GH32 = nullptr; double* GH64 = nullptr;
+  float* gram_part = nullptr;
+  // split-K
+  float* part = nullptr;
+  unsigned* counters = nullptr;
+  // objective
+  double* obj_parts = nullptr;
+  double* f_dev = nullptr;
+  double* f_host = nullptr;   // pinned
+  int* flag = nullptr;
+  int* err_dev = nullptr;     // device error word written by bounded waits
+  int* err_host = nullptr;    // pinned
+  HalfPlan half[2];           // [0] right update (H), [1] left update (W)
+  // CUDA-event timing by kind (nmf_profile_*)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_open;
+  double prof_ms[4] = {0, 0, 0, 0};
+  int64_t prof_n[4] = {0, 0, 0, 0};
+};
+
+namespace {
+
+nmf_status cuda_fail(nmf_ctx* c, cudaError_t e, const char* what) {
+  set_err(c ? &c->err : nullptr, "%s: %s", what, cudaGetErrorString(e));
+  return NMF_ECUDA;
+}
+
+#define CK(call, what)                                    \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+  } while (0)
+
+nmf_status dalloc(nmf_ctx* c, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    set_err(&c->err, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    return NMF_ENOMEM;
+  }
+  c->allocs.push_back(*p);
+  e = cudaMemsetAsync(*p, 0, bytes, c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
+  return NMF_OK;
+}
+
+bool is_aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+cudaEvent_t take_event(nmf_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) { (void)cudaGetLastError(); return nullptr; }
+  return e;
+}
+
+// Brackets one region of work of `kind` with events when profiling is on.
+struct ProfScope {
+  nmf_ctx* c;
+  int kind;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(nmf_ctx* c_, int k) : c(c_), kind(k) {
+    if (!c->prof) return;
+    a = take_event(c);
+    b = take_event(c);
+    if (a && b) cudaEventRecord(a, c->st);
+  }
+  ~ProfScope() {
+    if (!c->prof || !a || !b) return;
+    cudaEventRecord(b, c->st);
+    c->ev_open.push_back({kind, {a, b}});
+  }
+};
+
+void prof_collect(nmf_ctx* c) {
+  for (auto& it : c->ev_open) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, it.second.first, it.second.second) == cudaSuccess) {
+      c->prof_ms[it.first] += ms;
+      c->prof_n[it.first] += 1;
+    }
+    c->ev_pool.push_back(it.second.first);
+    c->ev_pool.push_back(it.second.second);
+  }
+  (void)cudaGetLastError();
+  c->ev_open.clear();
+}
+
+// Split-K plan: about `waves` resident blocks per SM over tiles x splits.
+void plan_split(HalfPlan& h, int block_m, int kblock, int sms, int waves, int user_split) {
+  h.tiles = (int)ceil_div(h.M, block_m);
+  int splits;
+  if (user_split > 0) {
+    splits = user_split;
+  } else {
+    const int64_t want = (int64_t)sms * waves;
+    splits = (int)ceil_div(want, h.tiles);
+    const int64_t max_by_k = ceil_div(h.K, (int64_t)kblock * 4);  // >= 4 k-blocks per split
+    if (splits > max_by_k) splits = (int)max_by_k;
+    if (splits < 1) splits = 1;
+  }
+  h.kchunk = round_up(ceil_div(h.K, splits), kblock);
+  h.splits = (int)ceil_div(h.K, h.kchunk);
+}
+
+nmf_status validate_cfg(const nmf_config* cfg) {
+  if (!cfg) { set_err(nullptr, "cfg is NULL"); return NMF_EINVAL; }
+  if (cfg->p < 1 || cfg->n < 1) { set_err(nullptr, "p and n must be >= 1"); return NMF_EINVAL; }
+  if (cfg->r < 1 || cfg->r > kMaxRank) {
+    set_err(nullptr, "rank r=%d outside 1..%d", cfg->r, kMaxRank);
+    return NMF_EINVAL;
+  }
+  if (cfg->r > cfg->p || cfg->r > cfg->n) {
+    set_err(nullptr, "rank r=%d exceeds min(p, n)", cfg->r);
+    return NMF_EINVAL;
+  }
+  if (!(cfg->eps >= 0.f) || isinf(cfg->eps)) { set_err(nullptr, "eps must be finite and >= 0"); return NMF_EINVAL; }
+  if (cfg->prec < NMF_FP32 || cfg->prec > NMF_BF16) { set_err(nullptr, "unknown precision"); return NMF_EINVAL; }
+  if (cfg->order != NMF_ORDER_H_FIRST && cfg->order != NMF_ORDER_W_FIRST) {
+    set_err(nullptr, "unknown order");
+    return NMF_EINVAL;
+  }
+  if (cfg->split_k < 0) { set_err(nullptr, "split_k must be >= 0"); return NMF_EINVAL; }
+  if (cfg->p > (int64_t)1 << 31 || cfg->n > (int64_t)1 << 31) {
+    set_err(nullptr, "p and n must be <= 2^31");
+    return NMF_EINVAL;
+  }
+  return NMF_OK;
+}
+
+// Operand copies of V, Algorithm 1's seeded start (optional), the factor
+// planes and the starting Gram matrices.  No allocation.
+nmf_status prepare(nmf_ctx* c, bool seed_factors, uint64_t seed) {
+  const int64_t p = c->p, n = c->n;
+  const int r = c->r;
+  cudaStream_t st = c->st;
+  ProfScope ps(c, 3);
+  if (c->plane == kPlaneF32 || c->plane == kPlaneTF32) {
+    const bool t32 = c->plane == kPlaneTF32;
+    if (c->Xw_hi != c->V) {
+      CK(launch_copy_pad(c->V, p, n, n, (float*)c->Xw_hi, c->ld_n, t32, st), "copy V");
+      launched(1);
+    }
+    CK(launch_transpose_pad(c->V, p, n, n, (float*)c->Xh_hi, c->ld_p, t32, st), "transpose V");
+    launched(1);
+  } else {
+    CK(launch_split_bf16(c->V, p, n, n, false, (__nv_bfloat16*)c->Xw_hi, (__nv_bfloat16*)c->Xw_lo,
+                         c->ld_n, st), "split V");
+    CK(launch_split_bf16(c->V, p, n, n, true, (__nv_bfloat16*)c->Xh_hi, (__nv_bfloat16*)c->Xh_lo,
+                         c->ld_p, st), "split V^T");
+    launched(2);
+  }
+  if (seed_factors) {
+    CK(launch_seed_uniform(c->W, p * r, seed, 1, st), "seed W");
+    CK(launch_seed_uniform(c->H, (int64_t)r * n, seed, 2, st), "seed H");
+    launched(2);
+  }
+  CK(launch_factor_planes(c->W, kFactorRowMajor, p, r, r, c->Wop_hi, c->Wop_lo, c->ld_p,
+                          c->plane, st), "W planes");
+  CK(launch_factor_planes(c->H, kFactorColMajor, n, n, r, c->Hop_hi, c->Hop_lo, c->ld_n,
+                          c->plane, st), "H planes");
+  CK(launch_gram_tiles(c->W, kFactorRowMajor, p, r, r, c->gram_part, 128, st), "gram W");
+  CK(launch_gram_reduce(c->gram_part, (int)ceil_div(p, 128), r, c->GW32, c->GW64, st),
+     "gram W reduce");
+  CK(launch_gram_tiles(c->H, kFactorColMajor, n, n, r, c->gram_part, 128, st), "gram H");
+  CK(launch_gram_reduce(c->gram_part, (int)ceil_div(n, 128), r, c->GH32, c->GH64, st),
+     "gram H reduce");
+  launched(6);
+  return NMF_OK;
+}
+
+nmf_status build_ctx(nmf_ctx* c) {
+  const int64_t p = c->p, n = c->n;
+  const int r = c->r;
+  const nmf_precision prec = c->cfg.prec;
+  const bool tc = prec != NMF_FP32;
+  cudaStream_t st = c->st;
+  int dev = 0;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev), "attr");
+  if (tc) {
+    int major = 0, minor = 0;
+    CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev), "attr");
+    CK(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev), "attr");
+    if (major != 10 || minor != 3) {
+      set_err(&c->err, "tensor-core precisions need an sm_103 GPU (found sm_%d%d)", major, minor);
+      return NMF_EUNSUPPORTED;
+    }
+  }
+  nmf_status s;
+  // Validation of V (optional): one pass.
+  if (c->cfg.validate) {
+    if ((s = dalloc(c, (void**)&c->flag, sizeof(int))) != NMF_OK) return s;
+    CK(launch_validate(c->V, p, n, c->flag, st), "validate");
+    launched(1);
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st), "memcpy");
+    CK(cudaStreamSynchronize(st), "sync");
+    if (h) {
+      set_err(&c->err, "V holds a negative or non-finite entry");
+      return NMF_ENONFINITE;
+    }
+  }
+  // Operand copies of V.
+  const bool bf = (prec == NMF_BF16X3 || prec == NMF_BF16);
+  const int elem = bf ? 2 : 4;
+  const int64_t align_el = 16 / elem;          // 16-byte rows (cp.async / TMA)
+  c->ld_n = round_up(n, align_el);
+  c->ld_p = round_up(p, align_el);
+  c->plane = (prec == NMF_BF16X3) ? kPlaneBF16x2
+             : (prec == NMF_BF16) ? kPlaneBF16 : (prec == NMF_TF32 ? kPlaneTF32 : kPlaneF32);
+  c->rpad = tc ? rank_pad16(r) : (int)round_up(r, 8);
+  if (!bf) {
+    if (prec == NMF_FP32 && n == c->ld_n && is_aligned16(c->V)) {
+      c->Xw_hi = c->V;
+    } else {
+      float* d;
+      if ((s = dalloc(c, (void**)&d, (size_t)p * c->ld_n * 4)) != NMF_OK) return s;
+      c->Xw_hi = d;
+    }
+    float* t;
+    if ((s = dalloc(c, (void**)&t, (size_t)n * c->ld_p * 4)) != NMF_OK) return s;
+    c->Xh_hi = t;
+  } else {
+    const bool lo = prec == NMF_BF16X3;
+    __nv_bfloat16 *a = nullptr, *b = nullptr, *ta = nullptr, *tb = nullptr;
+    if ((s = dalloc(c, (void**)&a, (size_t)p * c->ld_n * 2)) != NMF_OK) return s;
+    if ((s = dalloc(c, (void**)&ta, (size_t)n * c->ld_p * 2)) != NMF_OK) return s;
+    if (lo) {
+      if ((s = dalloc(c, (void**)&b, (size_t)p * c->ld_n * 2)) != NMF_OK) return s;
+      if ((s = dalloc(c, (void**)&tb, (size_t)n * c->ld_p * 2)) != NMF_OK) return s;
+    }
+    c->Xw_hi = a; c->Xw_lo = b; c->Xh_hi = ta; c->Xh_lo = tb;
+  }
+  // Factor planes (rpad rows; rows >= r stay zero).
+  {
+    const size_t wbytes = (size_t)c->rpad * c->ld_p * elem;
+    const size_t hbytes = (size_t)c->rpad * c->ld_n * elem;
+    if ((s = dalloc(c, &c->Wop_hi, wbytes)) != NMF_OK) return s;
+    if ((s = dalloc(c, &c->Hop_hi, hbytes)) != NMF_OK) return s;
+    if (c->plane == kPlaneBF16x2) {
+      if ((s = dalloc(c, &c->Wop_lo, wbytes)) != NMF_OK) return s;
+      if ((s = dalloc(c, &c->Hop_lo, hbytes)) != NMF_OK) return s;
+    }
+  }
+  // Grams.
+  const size_t rr = (size_t)r * r;
+  if ((s = dalloc(c, (void**)&c->GW32, rr * 4)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->GH32, rr * 4)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->GW64, rr * 8)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->GH64, rr * 8)) != NMF_OK) return s;
+
+  // Half-step plans.  [0]: right update (H) streams X = V^T (n x p) against
+  // Y = W^T; [1]: left update (W) streams X = V (p x n) against Y = H.
+  HalfPlan& hh = c->half[0];
+  HalfPlan& hw = c->half[1];
+  hh.X_hi = c->Xh_hi; hh.X_lo = c->Xh_lo; hh.ldx = c->ld_p;
+  hh.Y_hi = c->Wop_hi; hh.Y_lo = c->Wop_lo; hh.ldy = c->ld_p;
+  hh.M = n; hh.K = p;
+  hw.X_hi = c->Xw_hi; hw.X_lo = c->Xw_lo; hw.ldx = c->ld_n;
+  hw.Y_hi = c->Hop_hi; hw.Y_lo = c->Hop_lo; hw.ldy = c->ld_n;
+  hw.M = p; hw.K = n;
+
+  hh.ep.F = c->H; hh.ep.ldf = n; hh.ep.layout = kFactorColMajor; hh.ep.M = n;
+  hh.ep.op_hi = c->Hop_hi; hh.ep.op_lo = c->Hop_lo; hh.ep.ldop = c->ld_n;
+  hh.ep.G = c->GW32; hh.G32_out = c->GH32; hh.G64_out = c->GH64;
+  hw.ep.F = c->W; hw.ep.ldf = r; hw.ep.layout = kFactorRowMajor; hw.ep.M = p;
+  hw.ep.op_hi = c->Wop_hi; hw.ep.op_lo = c->Wop_lo; hw.ep.ldop = c->ld_p;
+  hw.ep.G = c->GH32; hw.G32_out = c->GW32; hw.G64_out = c->GW64;
+
+  size_t part_floats = 0, counters = 0, gram_tiles = 0;
+  for (HalfPlan* h : {&hh, &hw}) {
+    h->ep.r = r;
+    h->ep.eps = c->cfg.eps;
+    h->ep.plane = c->plane;
+    int bm;
+    if (!tc) {
+      bm = simt_block_m(r);
+      plan_split(*h, bm, 32, c->sms, 4, c->cfg.split_k);
+    } else {
+      s = tc_plan(c->cfg.prec, h->X_hi, h->X_lo, h->ldx, h->Y_hi, h->Y_lo, h->ldy, h->M, h->K, r,
+                  c->sms, c->cfg.split_k, &h->tc, &c->err);
+      if (s != NMF_OK) return s;
+      bm = h->tc.block_m;
+      h->tiles = h->tc.tiles;
+      h->splits = h->tc.splits;
+      h->kchunk = h->tc.kchunk;
+    }
+    const int rp_acc = tc ? c->rpad : (int)round_up(r, 8);
+    if (h->splits > 1) {
+      const size_t pf = (size_t)h->tiles * h->splits * bm * rp_acc;
+      if (pf > part_floats) part_floats = pf;
+    }
+    if ((size_t)h->tiles > counters) counters = h->tiles;
+    const size_t gt = ceil_div(h->M, 128) > h->tiles ? ceil_div(h->M, 128) : h->tiles;
+    if (gt > gram_tiles) gram_tiles = gt;
+  }
+  if ((s = dalloc(c, (void**)&c->part, part_floats * 4)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->counters, counters * 4)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->gram_part, gram_tiles * rr * 4)) != NMF_OK) return s;
+  for (HalfPlan* h : {&hh, &hw}) h->ep.gram_part = c->gram_part;
+  if ((s = dalloc(c, (void**)&c->obj_parts, objective_parts() * 8)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->f_dev, 8)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->err_dev, sizeof(int))) != NMF_OK) return s;
+  CK(cudaMallocHost((void**)&c->f_host, 8), "cudaMallocHost");
+  CK(cudaMallocHost((void**)&c->err_host, sizeof(int)), "cudaMallocHost");
+
+  return prepare(c, c->cfg.init_from_seed != 0, c->cfg.seed);
+}
+
+void free_ctx(nmf_ctx* c) {
+  if (!c) return;
+  if (c->st == nullptr || cudaStreamSynchronize(c->st) != cudaSuccess) (void)cudaDeviceSynchronize();
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->f_host) cudaFreeHost(c->f_host);
+  if (c->err_host) cudaFreeHost(c->err_host);
+  for (auto& it : c->ev_open) { cudaEventDestroy(it.second.first); cudaEventDestroy(it.second.second); }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  (void)cudaGetLastError();
+  delete c;
+}
+
+// Reads the device error word (synchronises).  A bounded device-side wait
+// that ran out reports NMF_ETIMEOUT here; the word is then cleared.
+nmf_status check_device_error(nmf_ctx* c) {
+  CK(cudaMemcpyAsync(c->err_host, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->st),
+     "memcpy err");
+  CK(cudaStreamSynchronize(c->st), "sync");
+  if (*c->err_host != 0) {
+    const int code = *c->err_host;
+    CK(cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->st), "memset err");
+    set_err(&c->err, "a bounded device wait expired (code %d); results are invalid", code);
+    return NMF_ETIMEOUT;
+  }
+  return NMF_OK;
+}
+
+nmf_status run_half(nmf_ctx* c, int which) {
+  HalfPlan& h = c->half[which];
+  SplitArgs sp{c->part, c->counters, h.splits, h.kchunk};
+  {
+  ProfScope ps(c, 0);
+  if (c->cfg.prec == NMF_FP32) {
+    CK(launch_stream_simt(static_cast<const float*>(h.X_hi), h.ldx,
+                          static_cast<const float*>(h.Y_hi), h.ldy, h.M, h.K, c->r, sp, h.ep,
+                          c->st), "stream (fp32)");
+  } else {
+    CK(tc_launch(h.tc, sp, h.ep, c->err_dev, c->st), "stream (tensor)");
+  }
+  launched(1);
+  }
+  ProfScope ps(c, 1);
+  CK(launch_gram_reduce(c->gram_part, h.tiles, c->r, h.G32_out, h.G64_out, c->st),
+     "gram reduce");
+  launched(1);
+  return NMF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nmf_status nmf_config_default(nmf_config* cfg, int64_t p, int64_t n, int32_t r) {
+  if (!cfg) { set_err(nullptr, "cfg is NULL"); return NMF_EINVAL; }
+  std::memset(cfg, 0, sizeof *cfg);
+  cfg->p = p; cfg->n = n; cfg->r = r;
+  cfg->eps = 1e-10f;
+  cfg->prec = NMF_FP32;
+  cfg->order = NMF_ORDER_H_FIRST;
+  return NMF_OK;
+}
+
+nmf_status nmf_init(const nmf_config* cfg, const float* V, float* W, float* H, void* stream,
+                    nmf_ctx** out) {
+  if (!out) { set_err(nullptr, "out is NULL"); return NMF_EINVAL; }
+  *out = nullptr;
+  nmf_status s = validate_cfg(cfg);
+  if (s != NMF_OK) return s;
+  if (!V || !W || !H) { set_err(nullptr, "V, W and H must be non-NULL"); return NMF_EINVAL; }
+  nmf_ctx* c = new (std::nothrow) nmf_ctx;
+  if (!c) { set_err(nullptr, "host allocation failed"); return NMF_ENOMEM; }
+  c->cfg = *cfg;
+  c->V = V; c->W = W; c->H = H;
+  c->st = static_cast<cudaStream_t>(stream);
+  c->p = cfg->p; c->n = cfg->n; c->r = cfg->r;
+  s = build_ctx(c);
+  if (s != NMF_OK) {
+    std::string why = c->err;
+    free_ctx(c);
+    g_last_error = why;
+    return s;
+  }
+  *out = c;
+  return NMF_OK;
+}
+
+nmf_status nmf_half_step(nmf_ctx* c, int which) {
+  if (!c) { set_err(nullptr, "ctx is NULL"); return NMF_EINVAL; }
+  if (which != 0 && which != 1) { set_err(&c->err, "which must be 0 (H) or 1 (W)"); return NMF_EINVAL; }
+  return run_half(c, which);
+}
+
+nmf_status nmf_step(nmf_ctx* c, int iters) {
+  if (!c) { set_err(nullptr, "ctx is NULL"); return NMF_EINVAL; }
+  if (iters < 0) { set_err(&c->err, "iters must be >= 0"); return NMF_EINVAL; }
+  const int first = c->cfg.order == NMF_ORDER_H_FIRST ? 0 : 1;
+  for (int it = 0; it < iters; ++it) {
+    nmf_status s = run_half(c, first);
+    if (s != NMF_OK) return s;
+    s = run_half(c, 1 - first);
+    if (s != NMF_OK) return s;
+  }
+  return NMF_OK;
+}
+
+nmf_status nmf_objective(nmf_ctx* c, double* f_out) {
+  if (!c || !f_out) { set_err(c ? &c->err : nullptr, "ctx and f_out must be non-NULL"); return NMF_EINVAL; }
+  {
+    ProfScope ps(c, 2);
+    CK(launch_objective(c->V, c->n, c->W, c->H, c->p, c->n, c->r, c->obj_parts,
+                        objective_parts(), c->f_dev, c->st), "objective");
+    launched(2);
+  }
+  CK(cudaMemcpyAsync(c->f_host, c->f_dev, 8, cudaMemcpyDeviceToHost, c->st), "memcpy f");
+  nmf_status s = check_device_error(c);
+  if (s != NMF_OK) return s;
+  *f_out = *c->f_host;
+  return NMF_OK;
+}
+
+nmf_status nmf_run(nmf_ctx* c, int max_iters, double tol, int check_every, int* iters_done,
+                   double* f_out) {
+  if (!c) { set_err(nullptr, "ctx is NULL"); return NMF_EINVAL; }
+  if (max_iters < 0 || check_every < 1 || !(tol >= 0.0)) {
+    set_err(&c->err, "need max_iters >= 0, check_every >= 1, tol >= 0");
+    return NMF_EINVAL;
+  }
+  double f_prev = 0.0, f = 0.0;
+  nmf_status s = nmf_objective(c, &f_prev);
+  if (s != NMF_OK) return s;
+  f = f_prev;
+  int done = 0;
+  while (done < max_iters) {
+    const int k = (max_iters - done) < check_every ? (max_iters - done) : check_every;
+    if ((s = nmf_step(c, k)) != NMF_OK) return s;
+    done += k;
+    if ((s = nmf_objective(c, &f)) != NMF_OK) return s;
+    // Section 3's rule: |f_k - f_{k-1}| / (|f_{k-1}| + 1) < tol
+    if (tol > 0.0 && std::fabs(f - f_prev) / (std::fabs(f_prev) + 1.0) < tol) break;
+    f_prev = f;
+  }
+  if (iters_done) *iters_done = done;
+  if (f_out) *f_out = f;
+  return NMF_OK;
+}
+
+nmf_status nmf_read_gram(nmf_ctx* c, int which, double* out) {
+  if (!c || !out || (which != 0 && which != 1)) {
+    set_err(c ? &c->err : nullptr, "bad argument to nmf_read_gram");
+    return NMF_EINVAL;
+  }
+  CK(cudaMemcpyAsync(out, which == 0 ? c->GW64 : c->GH64, (size_t)c->r * c->r * 8,
+                     cudaMemcpyDeviceToHost, c->st), "memcpy gram");
+  return check_device_error(c);
+}
+
+void nmf_destroy(nmf_ctx* c) { free_ctx(c); }
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { (void)cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+nmf_status nmf_solve(const nmf_config* cfg, const float* V, float* W, float* H, int iters,
+                     double* f_out, void* stream) {
+  nmf_status s = validate_cfg(cfg);
+  if (s != NMF_OK) return s;
+  if (!V || !W || !H || iters < 0) { set_err(nullptr, "bad argument to nmf_solve"); return NMF_EINVAL; }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t p = cfg->p, n = cfg->n, r = cfg->r;
+  const size_t vb = (size_t)p * n * 4, wb = (size_t)p * r * 4, hb = (size_t)r * n * 4;
+  const bool dv = is_device_ptr(V), dw = is_device_ptr(W), dh = is_device_ptr(H);
+  float *Vd = const_cast<float*>(V), *Wd = W, *Hd = H;
+  std::vector<void*> tmp;
+  auto cleanup = [&]() { for (void* q : tmp) cudaFree(q); };
+  auto fail = [&](cudaError_t e, const char* what) {
+    set_err(nullptr, "%s: %s", what, cudaGetErrorString(e));
+    cudaStreamSynchronize(st);
+    cleanup();
+    return NMF_ECUDA;
+  };
+  cudaError_t e;
+  if (!dv) { if ((e = cudaMalloc((void**)&Vd, vb)) != cudaSuccess) return fail(e, "cudaMalloc V"); tmp.push_back(Vd);
+             if ((e = cudaMemcpyAsync(Vd, V, vb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e, "H2D V"); }
+  if (!dw) { if ((e = cudaMalloc((void**)&Wd, wb)) != cudaSuccess) return fail(e, "cudaMalloc W"); tmp.push_back(Wd);
+             if ((e = cudaMemcpyAsync(Wd, W, wb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e, "H2D W"); }
+  if (!dh) { if ((e = cudaMalloc((void**)&Hd, hb)) != cudaSuccess) return fail(e, "cudaMalloc H"); tmp.push_back(Hd);
+             if ((e = cudaMemcpyAsync(Hd, H, hb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e, "H2D H"); }
+  nmf_ctx* c = nullptr;
+  s = nmf_init(cfg, Vd, Wd, Hd, stream, &c);
+  if (s == NMF_OK) s = nmf_step(c, iters);
+  if (s == NMF_OK && f_out) s = nmf_objective(c, f_out);
+  if (s == NMF_OK) {
+    if (!dw && (e = cudaMemcpyAsync(W, Wd, wb, cudaMemcpyDeviceToHost, st)) != cudaSuccess) { nmf_destroy(c); return fail(e, "D2H W"); }
+    if (!dh && (e = cudaMemcpyAsync(H, Hd, hb, cudaMemcpyDeviceToHost, st)) != cudaSuccess) { nmf_destroy(c); return fail(e, "D2H H"); }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { nmf_destroy(c); return fail(e, "sync"); }
+  }
+  std::string why = c ? c->err : g_last_error;
+  if (c) nmf_destroy(c);
+  cleanup();
+  if (s != NMF_OK) g_last_error = why;
+  return s;
+}
+
+nmf_status nmf_restart(nmf_ctx* c, uint64_t seed) {
+  if (!c) { set_err(nullptr, "ctx is NULL"); return NMF_EINVAL; }
+  return prepare(c, true, seed);
+}
+
+uint64_t nmf_kernel_launches(void) { return g_launches.load(); }
+
+nmf_status nmf_profile_enable(nmf_ctx* c, int on) {
+  if (!c) { set_err(nullptr, "ctx is NULL"); return NMF_EINVAL; }
+  if (on) {
+    CK(cudaStreamSynchronize(c->st), "sync");
+    prof_collect(c);
+    for (int k = 0; k < 4; ++k) { c->prof_ms[k] = 0; c->prof_n[k] = 0; }
+  }
+  c->prof = on != 0;
+  return NMF_OK;
+}
+
+nmf_status nmf_profile_read(nmf_ctx* c, int kind, double* ms, int64_t* count) {
+  if (!c || kind < 0 || kind > 3) { set_err(c ? &c->err : nullptr, "bad profile kind"); return NMF_EINVAL; }
+  CK(cudaStreamSynchronize(c->st), "sync");
+  prof_collect(c);
+  if (ms) *ms = c->prof_ms[kind];
+  if (count) *count = c->prof_n[kind];
+  return NMF_OK;
+}
+
+const char* nmf_status_str(nmf_status s) {
+  switch (s) {
+    case NMF_OK: return "NMF_OK";
+    case NMF_EINVAL: return "NMF_EINVAL: invalid argument";
+    case NMF_ENOMEM: return "NMF_ENOMEM: out of memory";
+    case NMF_ECUDA: return "NMF_ECUDA: CUDA error";
+    case NMF_ETIMEOUT: return "NMF_ETIMEOUT: bounded device wait expired";
+    case NMF_ENONFINITE: return "NMF_ENONFINITE: V has a negative or non-finite entry";
+    case NMF_EUNSUPPORTED: return "NMF_EUNSUPPORTED: not supported by this build/device";
+  }
+  return "unknown nmf_status";
+}
+
+const char* nmf_last_error(const nmf_ctx* c) { return c ? c->err.c_str() : g_last_error.c_str(); }
+
+const char* nmf_version(void) { return "nmf-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,34 @@
+// tcgen05 (5th-generation tensor core) form of the V-streaming products:
+// plan (tensor maps, tiling, split-K) and launch.  Implemented in k_stream_tc.cu.
+#pragma once
+
+#include <cuda.h>
+#include <string>
+
+#include "nmf_internal.cuh"
+
+namespace nmf {
+
+struct TcPlan {
+  int prec = 0;          // nmf_precision
+  int block_m = 128;     // rows of X per output tile (tcgen05 M)
+  int rpad = 16;         // accumulator columns (tcgen05 N), multiple of 16
+  int tiles = 0;
+  int splits = 1;
+  int64_t kchunk = 0;    // K per split, multiple of the k-block
+  int kblock = 64;       // K elements per pipeline stage
+  int64_t M = 0, K = 0;
+  int r = 0;
+  int grid = 0;
+  int smem = 0;
+  CUtensorMap x_hi, x_lo, y_hi, y_lo;
+};
+
+nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, const void* Y_hi,
+                   const void* Y_lo, int64_t ldy, int64_t M, int64_t K, int r, int sms,
+                   int user_split, TcPlan* plan, std::string* err);
+
+cudaError_t tc_launch(const TcPlan& plan, const SplitArgs& sp, const EpiArgs& ep, int* err,
+                      cudaStream_t st);
+
+}  // namespace nmf

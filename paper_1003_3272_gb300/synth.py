@@ -19,7 +19,7 @@ with GAMMA = 0x9E3779B97F4A7C15 and the SplitMix64 finaliser
 
 Distributions (all produced in float32 unless stated):
   * uniform on [0,1):   (word >> 40) * 2**-24                 exact in fp32
-  * uniform on (0,1):   ((word >> 40) + 0.5) * 2**-24         exact, never 0 or 1
+  * uniform on (0,1):   ((word >> 41) + 0.5) * 2**-23         exact, never 0 or 1
   * Exponential(1) = Gamma(1,1):  -log(((word >> 11) + 0.5) * 2**-53) in fp64,
     rounded once to fp32
   * |N(0, sigma^2)|:  Box-Muller on words 2i (radius) and 2i+1 (angle), fp64,
@@ -97,7 +97,7 @@ def _fill(seed, stream, count, fn, dtype=np.float32):
 def uniform_open(seed: int, stream: int, shape) -> np.ndarray:
     """iid uniform on (0,1), float32, row-major ``shape``."""
     n = int(np.prod(shape))
-    f = lambda w: ((w >> np.uint64(40)).astype(np.float64) + 0.5) * 2.0 ** -24
+    f = lambda w: ((w >> np.uint64(41)).astype(np.float64) + 0.5) * 2.0 ** -23
     return _fill(seed, stream, n, f).reshape(shape)
 
 

@@ -1,0 +1,91 @@
+"""Host-side checks of the C-ABI library: it loads, exports every symbol
+include/nmf.h declares, and rejects bad arguments before touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1003_3272_gb300 import build as nbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    nbuild.build()
+    from paper_1003_3272_gb300 import nmf
+    return nmf.load()
+
+
+def _declared():
+    names = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not f.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"\b(nmf_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "nmf_init" in names and "nmf_batched_step" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_the_header():
+    from paper_1003_3272_gb300 import nmf
+    assert sorted(nmf.EXPORTS) == _declared()
+
+
+def test_status_strings_and_version(lib):
+    for s in range(7):
+        assert lib.nmf_status_str(s).decode().startswith("NMF_")
+    assert b"sm_103a" in lib.nmf_version()
+
+
+def test_config_struct_layout(lib):
+    from paper_1003_3272_gb300 import nmf
+    cfg = nmf.Config()
+    assert lib.nmf_config_default(ctypes.byref(cfg), 10, 20, 3) == nmf.OK
+    assert (cfg.p, cfg.n, cfg.r) == (10, 20, 3)
+    assert cfg.eps == pytest.approx(1e-10)
+    assert cfg.prec == nmf.FP32 and cfg.order == nmf.H_FIRST
+    assert ctypes.sizeof(nmf.Config) == 56
+
+
+@pytest.mark.parametrize("bad", [
+    dict(r=0), dict(r=129), dict(r=30, p=20), dict(r=30, n=20), dict(eps=-1.0),
+    dict(eps=float("nan")), dict(prec=7), dict(order=5), dict(split_k=-2), dict(p=0),
+])
+def test_invalid_configs_are_rejected_on_the_host(lib, bad):
+    from paper_1003_3272_gb300 import nmf
+    args = dict(p=100, n=120, r=10)
+    args.update({k: v for k, v in bad.items() if k in ("p", "n", "r")})
+    cfg = nmf.Config()
+    lib.nmf_config_default(ctypes.byref(cfg), args["p"], args["n"], args["r"])
+    for k in ("eps", "prec", "order", "split_k"):
+        if k in bad:
+            setattr(cfg, k, bad[k])
+    ctx = ctypes.c_void_p(123)
+    dummy = ctypes.c_void_p(16)
+    st = lib.nmf_init(ctypes.byref(cfg), dummy, dummy, dummy, None, ctypes.byref(ctx))
+    assert st == nmf.EINVAL
+    assert ctx.value is None
+    assert len(lib.nmf_last_error(None)) > 0
+
+
+def test_null_pointers_rejected(lib):
+    from paper_1003_3272_gb300 import nmf
+    cfg = nmf.Config()
+    lib.nmf_config_default(ctypes.byref(cfg), 10, 10, 2)
+    ctx = ctypes.c_void_p()
+    assert lib.nmf_init(ctypes.byref(cfg), None, None, None, None, ctypes.byref(ctx)) == nmf.EINVAL
+    assert lib.nmf_init(None, None, None, None, None, ctypes.byref(ctx)) == nmf.EINVAL
+    assert lib.nmf_step(None, 1) == nmf.EINVAL
+    assert lib.nmf_objective(None, None) == nmf.EINVAL
+    assert lib.nmf_half_step(None, 0) == nmf.EINVAL
+    lib.nmf_destroy(None)  # no-op

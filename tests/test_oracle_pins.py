@@ -316,7 +316,12 @@ def test_distributions():
     a = synth.uniform_open(9, 1, (5000000,))
     b = synth.words(9, 1, 4194300, 10)
     assert np.array_equal(a[4194300:4194310],
-                          (((b >> np.uint64(40)).astype(np.float64) + 0.5) * 2.0 ** -24).astype(np.float32))
+                          (((b >> np.uint64(41)).astype(np.float64) + 0.5) * 2.0 ** -23).astype(np.float32))
+    # the extreme words map strictly inside (0, 1), exactly
+    top = np.array([np.uint64(2**64 - 1), np.uint64(0)])
+    ext = (((top >> np.uint64(41)).astype(np.float64) + 0.5) * 2.0 ** -23).astype(np.float32)
+    assert ext[0] < 1.0 and ext[1] > 0.0
+    assert float(ext[0]) == 1.0 - 2.0 ** -24 and float(ext[1]) == 2.0 ** -24
 
 
 # --- planted mistakes: each plausible slip in the oracle fails a pin ------------------
