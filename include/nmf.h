@@ -162,6 +162,26 @@ nmf_status nmf_batched_step(nmf_batch* b, int iters);
 nmf_status nmf_batched_objective(nmf_batch* b, double* f_out);
 void nmf_batched_destroy(nmf_batch* b);
 
+/* ---- Gram matrix without allocation --------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc -- programs whose device memory belongs to
+ * another allocator (a framework's caching allocator or a fixed arena), and
+ * latency-critical code where cudaMalloc may synchronise the device.
+ * Computes, on `stream`, the r x r Gram matrix of a factor F with the same
+ * kernels nmf_init uses, writing float64 G_out (device, r*r, row-major):
+ *   layout 0: F is M x r row-major (ldf must equal r), G = F^T F   (like W)
+ *   layout 1: F is r x M with row pitch ldf >= M,      G = F F^T   (like H)
+ * It allocates nothing: its scratch is a static 8 MiB device array inside
+ * the library, held by every GPU that loads the library until exit.  The
+ * first call on a device (with that device current) looks the array's
+ * device address up; make that first call before any stream capture.
+ * Sizes needing more than 2^21 floats of scratch (ceil(M/128)*r*r + r*r)
+ * are rejected with NMF_EINVAL and a message in nmf_last_error(NULL).  All
+ * calls share the scratch: calls that overlap on the GPU race and must not
+ * be issued concurrently.  Asynchronous.                                    */
+nmf_status nmf_gram_noalloc(const float* F, int32_t layout, int64_t M, int64_t ldf, int32_t r,
+                            double* G_out, void* stream);
+
 /* ---- Instrumentation ---------------------------------------------------
  * Number of kernels this library has launched in this process (all
  * contexts), for launch accounting.                                         */

@@ -33,6 +33,11 @@ void set_err(std::string* dst, const char* fmt, ...) {
 
 }  // namespace
 
+namespace nmf {
+void record_error(const char* msg) { g_last_error = msg; }
+void count_launches(int k) { launched(k); }
+}  // namespace nmf
+
 // One V-streaming product followed by its fused epilogue: which operands,
 // which factor, which workspace.
 struct HalfPlan {

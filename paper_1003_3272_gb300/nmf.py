@@ -44,7 +44,7 @@ EXPORTS = [
     "nmf_run", "nmf_read_gram", "nmf_solve", "nmf_destroy", "nmf_batched_init",
     "nmf_batched_step", "nmf_batched_objective", "nmf_batched_destroy",
     "nmf_status_str", "nmf_last_error", "nmf_version", "nmf_restart",
-    "nmf_kernel_launches", "nmf_profile_enable", "nmf_profile_read",
+    "nmf_kernel_launches", "nmf_profile_enable", "nmf_profile_read", "nmf_gram_noalloc",
 ]
 
 _lib = None
@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "nmf_version": ([], ctypes.c_char_p),
         "nmf_restart": ([c_p, ctypes.c_uint64], ctypes.c_int),
         "nmf_kernel_launches": ([], ctypes.c_uint64),
+        "nmf_gram_noalloc": ([c_p, i32, i64, i64, i32, c_p, c_p], ctypes.c_int),
         "nmf_profile_enable": ([c_p, ctypes.c_int], ctypes.c_int),
         "nmf_profile_read": ([c_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
