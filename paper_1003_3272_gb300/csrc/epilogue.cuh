@@ -20,10 +20,10 @@
 
 namespace nmf {
 
-// Shared-memory floats needed by mu_epilogue for a BM x RPAD tile.
-template <int BM, int RPAD>
-constexpr int epi_smem_floats() {
-  return 2 * BM * (RPAD + 1) + RPAD * RPAD;
+// Shared-memory floats needed by mu_epilogue for an R x RPAD slice.
+template <int RPAD>
+__host__ __device__ constexpr int epi_smem_floats(int R) {
+  return 2 * R * (RPAD + 1) + RPAD * RPAD;
 }
 
 __device__ __forceinline__ void store_plane(const EpiArgs& e, int k, int64_t m, float v) {
@@ -42,41 +42,75 @@ __device__ __forceinline__ void store_plane(const EpiArgs& e, int k, int64_t m, 
   }
 }
 
-// Ns: [BM][RPAD+1] holds the final numerator tile on entry (rows >= M - m0
-//     are ignored) and the new factor tile on exit.
-// Os: [BM][RPAD+1] scratch for the old factor tile.
-// Gs: [RPAD][RPAD] scratch for the Gram matrix.
+// Multiply-divide update of an R-row slice of a tile whose first row is
+// global row `row0` (rows beyond e.M are ignored).
+// Ns: [R][RPAD+1] holds the final numerator slice on entry and the new
+//     factor slice on exit.
+// Os: [R][RPAD+1] scratch for the old factor slice.
+// Gs: [RPAD][RPAD] scratch, filled here from e.G (the other factor's Gram,
+//     read through L2: it may have been written earlier in the same launch).
+// P : r x r destination of the slice's partial Gram of the new factor.
 // All NT threads of the block must call it.
-template <int BM, int RPAD, int NT>
-__device__ void mu_epilogue(float* Ns, float* Os, float* Gs, int64_t m0, int tile,
+template <int RPAD, int NT>
+__device__ void mu_epilogue(float* Ns, float* Os, float* Gs, int R, int64_t row0, float* P,
                             const EpiArgs& e) {
   constexpr int LD = RPAD + 1;
   const int tid = threadIdx.x;
   const int r = e.r;
   const int64_t M = e.M;
-  const int rows = (int)((M - m0) < BM ? (M - m0) : BM);
+  const int rows = (int)((M - row0) < R ? (M - row0 > 0 ? M - row0 : 0) : R);
 
-  for (int i = tid; i < RPAD * RPAD; i += NT) {
-    const int l = i / RPAD, k = i % RPAD;
-    Gs[i] = (l < r && k < r) ? e.G[l * r + k] : 0.f;
+  // Loads are issued eight at a time before any use, so a thread waits for
+  // one memory round trip per eight values instead of one per value.
+  for (int b = tid; b < RPAD * RPAD; b += 8 * NT) {
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = b + j * NT;
+      const int l = i / RPAD, k = i % RPAD;
+      v[j] = (i < RPAD * RPAD && l < r && k < r) ? __ldcg(e.G + l * r + k) : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (b + j * NT < RPAD * RPAD) Gs[b + j * NT] = v[j];
   }
   if (e.layout == kFactorRowMajor) {
-    for (int i = tid; i < BM * RPAD; i += NT) {
-      const int m = i / RPAD, k = i % RPAD;
-      Os[m * LD + k] = (m < rows && k < r) ? e.F[(m0 + m) * r + k] : 0.f;
+    for (int b = tid; b < R * RPAD; b += 8 * NT) {
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int i = b + j * NT;
+        const int m = i / RPAD, k = i % RPAD;
+        v[j] = (i < R * RPAD && m < rows && k < r) ? e.F[(row0 + m) * r + k] : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int i = b + j * NT;
+        if (i < R * RPAD) Os[(i / RPAD) * LD + (i % RPAD)] = v[j];
+      }
     }
   } else {
-    for (int i = tid; i < BM * RPAD; i += NT) {
-      const int k = i / BM, m = i % BM;
-      Os[m * LD + k] = (m < rows && k < r) ? e.F[(int64_t)k * e.ldf + m0 + m] : 0.f;
+    for (int b = tid; b < R * RPAD; b += 8 * NT) {
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int i = b + j * NT;
+        const int k = i / R, m = i % R;
+        v[j] = (i < R * RPAD && m < rows && k < r) ? e.F[(int64_t)k * e.ldf + row0 + m] : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int i = b + j * NT;
+        if (i < R * RPAD) Os[(i % R) * LD + (i / R)] = v[j];
+      }
     }
   }
   __syncthreads();
 
   // new = old * num / (old . G[:, k] + eps), eight ranks per work item.
   constexpr int KG = RPAD / 8;
-  for (int it = tid; it < BM * KG; it += NT) {
-    const int m = it % BM, kg = it / BM;
+  for (int it = tid; it < R * KG; it += NT) {
+    const int m = it % R, kg = it / R;
     float den[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) den[j] = 0.f;
@@ -106,24 +140,22 @@ __device__ void mu_epilogue(float* Ns, float* Os, float* Gs, int64_t m0, int til
   if (e.layout == kFactorRowMajor) {
     for (int i = tid; i < rows * r; i += NT) {
       const int m = i / r, k = i % r;
-      e.F[(m0 + m) * r + k] = Ns[m * LD + k];
+      e.F[(row0 + m) * r + k] = Ns[m * LD + k];
     }
   } else {
     for (int i = tid; i < rows * r; i += NT) {
       const int k = i / rows, m = i % rows;
-      e.F[(int64_t)k * e.ldf + m0 + m] = Ns[m * LD + k];
+      e.F[(int64_t)k * e.ldf + row0 + m] = Ns[m * LD + k];
     }
   }
   for (int i = tid; i < rows * r; i += NT) {
     const int k = i / rows, m = i % rows;
-    store_plane(e, k, m0 + m, Ns[m * LD + k]);
+    store_plane(e, k, row0 + m, Ns[m * LD + k]);
   }
 
-  // Partial Gram of the new tile: P[k][l] = sum_m new[m,k] new[m,l], k <= l.
-  float* P = e.gram_part + (int64_t)tile * r * r;
+  // Partial Gram of the new slice: P[k][l] = sum_m new[m,k] new[m,l], k <= l.
   const int npairs = r * (r + 1) / 2;
   for (int it = tid; it < npairs; it += NT) {
-    // unrank (k, l) with k <= l
     int k = 0, rem = it;
     while (rem >= r - k) { rem -= r - k; ++k; }
     const int l = k + rem;

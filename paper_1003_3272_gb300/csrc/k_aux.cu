@@ -86,6 +86,43 @@ __global__ void k_split_bf16(const float* __restrict__ src, int64_t rows, int64_
   }
 }
 
+// Tile-blocked operand copy of V for the tensor-core products.  The output
+// is the M x K matrix (V itself, or V^T when `transpose`) cut into blocks of
+// 128 rows x KBE columns (KBE = 64 bf16 or 32 tf32 = 128 bytes); block
+// (mt, kb) is stored contiguously (row pitch 128 bytes) at block index
+// mt * nkb + kb, so one tile's K range is a single contiguous stream.
+// mode 0: bf16 hi (and lo = bf16(v - hi) when lo != null); mode 1: tf32.
+// Entries outside M x K are never written (the buffer starts zeroed).
+__global__ void k_operand_blocked(const float* __restrict__ src, int64_t rows, int64_t cols,
+                                  int64_t lds, int transpose, int mode, void* __restrict__ hi,
+                                  void* __restrict__ lo, int64_t nkb, int kbe) {
+  __shared__ float t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t r = r0 + y, c = c0 + threadIdx.x;
+    t[y][threadIdx.x] = (r < rows && c < cols) ? src[r * lds + c] : 0.f;
+  }
+  __syncthreads();
+  const int64_t M = transpose ? cols : rows, K = transpose ? rows : cols;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    int64_t m, k;
+    float v;
+    if (transpose) { m = c0 + y; k = r0 + threadIdx.x; v = t[threadIdx.x][y]; }
+    else           { m = r0 + y; k = c0 + threadIdx.x; v = t[y][threadIdx.x]; }
+    if (m >= M || k >= K) continue;
+    const int64_t off = (((m >> 7) * nkb + k / kbe) * 128 + (m & 127)) * kbe + (k % kbe);
+    if (mode == 1) {
+      static_cast<float*>(hi)[off] = round_tf32(v);
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      static_cast<__nv_bfloat16*>(hi)[off] = h;
+      if (lo)
+        static_cast<__nv_bfloat16*>(lo)[off] =
+            __float2bfloat16_rn(__fsub_rn(v, __bfloat162float(h)));
+    }
+  }
+}
+
 // Operand plane(s) [k][m] of a factor: W (row-major p x r, plane = W^T) or
 // H (r x n, plane = H itself), in the precision of the streaming product.
 __global__ void k_factor_planes(const float* __restrict__ F, int layout, int64_t M,
@@ -334,6 +371,15 @@ cudaError_t launch_split_bf16(const float* src, int64_t rows, int64_t cols, int6
   dim3 grid((unsigned)ceil_div(gc, 32), (unsigned)ceil_div(gr, 32));
   k_split_bf16<<<grid, dim3(32, 8), 0, st>>>(src, rows, cols, lds, transpose ? 1 : 0, hi, lo,
                                               ldd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_operand_blocked(const float* src, int64_t rows, int64_t cols, int64_t lds,
+                                   bool transpose, bool tf32, void* hi, void* lo, int64_t nkb,
+                                   int kbe, cudaStream_t st) {
+  dim3 grid((unsigned)ceil_div(cols, 32), (unsigned)ceil_div(rows, 32));
+  k_operand_blocked<<<grid, dim3(32, 8), 0, st>>>(src, rows, cols, lds, transpose ? 1 : 0,
+                                                   tf32 ? 1 : 0, hi, lo, nkb, kbe);
   return cudaGetLastError();
 }
 

@@ -160,14 +160,15 @@ k_stream_simt(const SimtParams a) {
     if (tid == 0) a.sp.counters[tile] = 0u;  // ready for the next launch
   }
   __syncthreads();
-  mu_epilogue<BM, RPAD, kThreads>(Ns, Os, Gs, m0, tile, a.ep);
+  mu_epilogue<RPAD, kThreads>(Ns, Os, Gs, BM, m0, a.ep.gram_part + (int64_t)tile * a.r * a.r,
+                              a.ep);
 }
 
 template <int TM, int TR>
 cudaError_t launch_t(const SimtParams& p, cudaStream_t st) {
   constexpr int BM = 16 * TM, RPAD = 8 * TR;
   const size_t stage = (size_t)kStages * (BM + RPAD) * kLDS * sizeof(float);
-  const size_t epi = (size_t)epi_smem_floats<BM, RPAD>() * sizeof(float);
+  const size_t epi = (size_t)epi_smem_floats<RPAD>(BM) * sizeof(float);
   const size_t smem = stage > epi ? stage : epi;
   auto kern = k_stream_simt<TM, TR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

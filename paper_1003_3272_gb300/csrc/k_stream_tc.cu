@@ -1,22 +1,36 @@
 // Tensor-core (tcgen05) form of the two V-streaming products of an MM
 // iteration (Section 3.1: the numerators V H^T of Eq. (3.3) and W^T V of
-// Eq. (3.4)), for the TF32, split-BF16x3 and BF16 precisions.
+// Eq. (3.4)), for the TF32, split-BF16x3 and BF16 precisions, with the
+// multiply-divide update fused behind them.
 //
 // Both products are D[M x r] = X[M x K] . Y[r x K]^T with X and Y K-major
-// (see k_stream_simt.cu for the operand roles).  A block owns a 128-row tile
-// of X and one K-range (split-K):
-//   warp 0, one lane : TMA producer.  Each pipeline stage holds 128 bytes of
-//                      K (64 bf16 or 32 tf32 values) of the X tile (128 rows)
-//                      and of the Y tile (RPAD rows), 128-byte swizzled.
-//   warp 1, one lane : MMA issuer.  tcgen05.mma M=128, N=RPAD, K=32 bytes
-//                      per instruction into a float32 accumulator in tensor
-//                      memory; BF16x3 issues hi*hi + hi*lo + lo*hi.
-//   all 4 warps      : read the accumulator (warp w owns TMEM lanes 32w..),
-//                      then the split-K reduction (last block of a tile, in
-//                      split order) and the fused multiply-divide epilogue.
+// (see k_stream_simt.cu for the operand roles).
+//
+// Work decomposition.  A thread-block cluster of S blocks (S = 1, 2, 4, 8)
+// owns one 128-row tile of X at a time and splits its K range evenly; the
+// grid is persistent (at most the co-resident number of clusters) and a
+// cluster walks the tiles g, g + G, g + 2G, ...  Per block:
+//   warp 0, one lane : TMA producer.  A stage holds 128 bytes of K (64 bf16
+//                      or 32 tf32 values) of the X tile (128 rows) and of
+//                      the Y tile (RPAD rows), 128-byte swizzled.
+//   warp 1, one lane : MMA issuer, tcgen05.mma M=128, N=RPAD, 32 bytes of K
+//                      per instruction, float32 accumulator in tensor memory;
+//                      BF16x3 issues hi*hi + hi*lo + lo*hi.
+//   warps 2-3        : in the prologue, this block's share of the Gram matrix
+//                      of the *other* factor (float64 sum of the previous
+//                      half step's per-slice partials, fixed order), published
+//                      through a grid-wide counter.
+//   all 4 warps      : tile epilogue -- accumulator to shared memory; the
+//                      cluster reduces the S partial tiles over distributed
+//                      shared memory in rank order (deterministic), each block
+//                      taking 128/S rows; then the fused multiply-divide update
+//                      of its rows, the operand planes of the new factor and
+//                      the rows' partial Gram.
 // Every wait is bounded: on a timeout the block records NMF_ETIMEOUT in the
 // error word, lets its copies and MMAs drain, frees its tensor memory and
 // returns.
+#include <cooperative_groups.h>
+
 #include <cstdio>
 #include <mutex>
 
@@ -24,23 +38,34 @@
 #include "tc.cuh"
 #include "tc_ptx.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace nmf {
 namespace {
 
 constexpr int kThreads = 128;
 constexpr int kBM = 128;
-constexpr uint64_t kWaitLimitNs = 1500ull * 1000 * 1000;  // 1.5 s
+constexpr uint64_t kWaitLimitNs = 1500ull * 1000 * 1000;      // 1.5 s (global timer)
+constexpr uint64_t kWaitLimitCycles = 3000ull * 1000 * 1000;  // ~1.5 s at 2 GHz
 constexpr int kSmemBudget = 200 * 1024;
 
 struct TcParams {
   int64_t M, K;
   int r;
-  int splits;
-  int64_t kchunk;
-  float* part;           // [tiles][splits][RPAD][128] partial numerators
-  unsigned* counters;    // [tiles]
-  EpiArgs ep;
-  int* err;              // device error word (NMF_ETIMEOUT on a timeout)
+  int S;                 // cluster size = K-splits per tile
+  int tiles;
+  int nclusters;
+  int64_t kper;          // K per split (multiple of the k-block)
+  int nkbt;              // k-blocks per tile row (blocked X layout)
+  EpiArgs ep;            // ep.gram_part: this launch's slice partials [tiles*S][r][r]
+  // Gram of the other factor, reduced in the prologue
+  const float* gin;      // partials [gin_count][r][r]
+  int gin_count;
+  float* G32;            // r x r outputs (ep.G aliases G32)
+  double* G64;
+  unsigned long long* gctr;   // grid-wide publication counter
+  unsigned long long gtarget; // value meaning "every block of this launch published"
+  int* err;              // device error word
 };
 
 template <int PREC>
@@ -55,7 +80,12 @@ struct TcShape {
   static constexpr int X_BYTES = kBM * 128;       // one plane of X: 128 rows x 128 B
   static constexpr int Y_BYTES = RPAD * 128;      // one plane of Y
   static constexpr int STAGE = XPL * (X_BYTES + Y_BYTES);
-  static constexpr int EPI = epi_smem_floats<kBM, RPAD>() * 4;
+  static constexpr int LDA = RPAD + 4;            // accumulator tile row stride (floats)
+  static constexpr int ACC = kBM * LDA * 4;
+  // epilogue region: [Acc (S > 1)] [Ns | Os | Gs for up to 128 rows]
+  static constexpr int EPI1 = epi_smem_floats<RPAD>(kBM) * 4;           // S = 1
+  static constexpr int EPI2 = ACC + epi_smem_floats<RPAD>(kBM / 2) * 4; // S >= 2
+  static constexpr int EPI = EPI1 > EPI2 ? EPI1 : EPI2;
   static constexpr int STAGES_RAW = kSmemBudget / STAGE;
   static constexpr int STAGES = STAGES_RAW > 8 ? 8 : (STAGES_RAW < 2 ? 2 : STAGES_RAW);
   static constexpr int MAIN = STAGES * STAGE;
@@ -63,16 +93,24 @@ struct TcShape {
   static constexpr int TMEM_COLS = RPAD <= 32 ? 32 : (RPAD <= 64 ? 64 : 128);
 };
 
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
 template <int PREC, int RPAD>
 __global__ void __launch_bounds__(kThreads, 1)
 k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ CUtensorMap tx_lo,
             const __grid_constant__ CUtensorMap ty_hi, const __grid_constant__ CUtensorMap ty_lo,
             const TcParams a) {
-  using S = TcShape<PREC, RPAD>;
-  constexpr int STAGES = S::STAGES;
+  using Sh = TcShape<PREC, RPAD>;
+  constexpr int STAGES = Sh::STAGES;
   constexpr int KB = PrecTraits<PREC>::KB;
   constexpr bool X3 = PREC == NMF_BF16X3;
   constexpr uint32_t IDESC = ptx::idesc(PrecTraits<PREC>::FMT, kBM, RPAD);
+  constexpr int LDA = Sh::LDA;
+  constexpr int LD = RPAD + 1;
 
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
@@ -80,22 +118,19 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
   __shared__ __align__(8) uint64_t acc_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_abort;
-  __shared__ int s_last;
 
+  cg::cluster_group cluster = cg::this_cluster();
+  const int S = a.S;
+  const int q = (int)cluster.block_rank();
+  const int cid = blockIdx.x / S;          // cluster index
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = ptx::smem_u32(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x, split = blockIdx.y;
-  const int64_t m0 = (int64_t)tile * kBM;
-  const int64_t kbeg = (int64_t)split * a.kchunk;
-  const int64_t kend = min(a.K, kbeg + a.kchunk);
-  const int nkb = kbeg < kend ? (int)ceil_div(kend - kbeg, KB) : 0;
 
-  // stage s: [X_hi | X_lo | Y_hi | Y_lo]
-  auto x_addr = [&](int s, int plane) { return sbase + s * S::STAGE + plane * S::X_BYTES; };
+  auto x_addr = [&](int s, int plane) { return sbase + s * Sh::STAGE + plane * Sh::X_BYTES; };
   auto y_addr = [&](int s, int plane) {
-    return sbase + s * S::STAGE + S::XPL * S::X_BYTES + plane * S::Y_BYTES;
+    return sbase + s * Sh::STAGE + Sh::XPL * Sh::X_BYTES + plane * Sh::Y_BYTES;
   };
 
   if (threadIdx.x == 0) {
@@ -111,7 +146,7 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
     if (X3) { ptx::tma_prefetch(&tx_lo); ptx::tma_prefetch(&ty_lo); }
   }
   if (warp == 1) {
-    ptx::tmem_alloc(ptx::smem_u32(&tmem_slot), S::TMEM_COLS);
+    ptx::tmem_alloc(ptx::smem_u32(&tmem_slot), Sh::TMEM_COLS);
     ptx::tmem_relinquish();
   }
   ptx::tc_fence_before();
@@ -119,127 +154,210 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
   ptx::tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer ----------------
-    int issued = 0;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (!ptx::mbar_wait(ptx::smem_u32(&empty_bar[s]), ph ^ 1u, kWaitLimitNs)) {
-        atomicExch(&s_abort, 1);
-        break;
-      }
-      if (*(volatile int*)&s_abort) break;
-      const uint32_t fb = ptx::smem_u32(&full_bar[s]);
-      ptx::mbar_expect_tx(fb, S::STAGE);
-      const int32_t kc = (int32_t)(kbeg + (int64_t)kb * KB);
-      ptx::tma_load_2d(x_addr(s, 0), &tx_hi, kc, (int32_t)m0, fb);
-      if (X3) ptx::tma_load_2d(x_addr(s, 1), &tx_lo, kc, (int32_t)m0, fb);
-      ptx::tma_load_2d(y_addr(s, 0), &ty_hi, kc, 0, fb);
-      if (X3) ptx::tma_load_2d(y_addr(s, 1), &ty_lo, kc, 0, fb);
-      issued = kb + 1;
-    }
-    // Drain: the last load issued into each stage must have landed before
-    // this block may exit (normal path: already consumed, returns at once).
-    for (int kb = issued - 1; kb >= 0 && kb >= issued - STAGES; --kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[s]), ph, kWaitLimitNs)) atomicExch(&s_abort, 1);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer ----------------
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[s]), ph, kWaitLimitNs)) {
-        atomicExch(&s_abort, 1);
-        break;
-      }
-      if (*(volatile int*)&s_abort) break;
-      ptx::tc_fence_after();
+  // K range of this block (same for every tile).
+  const int64_t kbeg = (int64_t)q * a.kper;
+  const int64_t kend = min(a.K, kbeg + a.kper);
+  const int nkb = kbeg < kend ? (int)ceil_div(kend - kbeg, KB) : 0;
+
+  // ---- prologue: this block's share of the other factor's Gram ------------
+  if (warp >= 2) {
+    // Four entries per warp at a time, each lane summing every 32nd partial
+    // (loads issued together), then a fixed shuffle tree per entry.
+    const int rr = a.r * a.r;
+    const int nblk = gridDim.x;
+    const int e0 = (int)((int64_t)blockIdx.x * rr / nblk);
+    const int e1 = (int)((int64_t)(blockIdx.x + 1) * rr / nblk);
+    for (int eb = e0 + 4 * (warp - 2); eb < e1; eb += 8) {
+      double s4[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int t = lane; t < a.gin_count; t += 32) {
+        float v[4];
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const uint64_t ah = ptx::sdesc_sw128(x_addr(s, 0) + kk * 32);
-        const uint64_t bh = ptx::sdesc_sw128(y_addr(s, 0) + kk * 32);
-        const uint32_t acc = (kb | kk) != 0;
-        if (PREC == NMF_TF32) {
-          ptx::mma_tf32(tmem, ah, bh, IDESC, acc);
-        } else {
-          ptx::mma_bf16(tmem, ah, bh, IDESC, acc);
-          if (X3) {
-            const uint64_t al = ptx::sdesc_sw128(x_addr(s, 1) + kk * 32);
-            const uint64_t bl = ptx::sdesc_sw128(y_addr(s, 1) + kk * 32);
-            ptx::mma_bf16(tmem, ah, bl, IDESC, 1);
-            ptx::mma_bf16(tmem, al, bh, IDESC, 1);
+        for (int j = 0; j < 4; ++j)
+          v[j] = (eb + j < e1) ? __ldcg(a.gin + (int64_t)t * rr + eb + j) : 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s4[j] += (double)v[j];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) s4[j] += __shfl_down_sync(0xffffffffu, s4[j], o);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (eb + j < e1) {
+            a.G64[eb + j] = s4[j];
+            a.G32[eb + j] = (float)s4[j];
+          }
+      }
+    }
+    __threadfence();
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    if (threadIdx.x == 64) atomicAdd(a.gctr, 1ull);
+  }
+
+  int it = 0;        // tiles processed by this block
+  int kb_base = 0;   // k-blocks processed by this block (ring position)
+  bool gram_ready = false;
+  for (int tile = cid; tile < a.tiles; tile += a.nclusters, ++it) {
+    const int64_t m0 = (int64_t)tile * kBM;
+    const int nkb_run = *(volatile int*)&s_abort ? 0 : nkb;
+    if (warp == 0 && lane == 0) {
+      // ---------------- TMA producer ----------------
+      int issued = 0;
+      for (int kb = 0; kb < nkb_run; ++kb) {
+        const int g = kb_base + kb;
+        const int s = g % STAGES;
+        const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+        if (!ptx::mbar_wait(ptx::smem_u32(&empty_bar[s]), ph ^ 1u, kWaitLimitCycles)) {
+          atomicExch(&s_abort, 1);
+          break;
+        }
+        if (*(volatile int*)&s_abort) break;
+        const uint32_t fb = ptx::smem_u32(&full_bar[s]);
+        ptx::mbar_expect_tx(fb, Sh::STAGE);
+        const int32_t kc = (int32_t)(kbeg + (int64_t)kb * KB);
+        // X block (tile, k-block) of the tile-blocked copy: one contiguous 16 KB
+        const int32_t xb = (int32_t)((int64_t)tile * a.nkbt + kbeg / KB + kb);
+        ptx::tma_load_3d(x_addr(s, 0), &tx_hi, 0, 0, xb, fb);
+        if (X3) ptx::tma_load_3d(x_addr(s, 1), &tx_lo, 0, 0, xb, fb);
+        ptx::tma_load_2d(y_addr(s, 0), &ty_hi, kc, 0, fb);
+        if (X3) ptx::tma_load_2d(y_addr(s, 1), &ty_lo, kc, 0, fb);
+        issued = kb + 1;
+      }
+      // Drain: the last load issued into each stage must have landed.
+      for (int kb = issued - 1; kb >= 0 && kb >= issued - STAGES; --kb) {
+        const int g = kb_base + kb;
+        if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[g % STAGES]), (uint32_t)(g / STAGES) & 1u,
+                            kWaitLimitCycles))
+          atomicExch(&s_abort, 1);
+      }
+    } else if (warp == 1 && lane == 0) {
+      // ---------------- MMA issuer ----------------
+      for (int kb = 0; kb < nkb_run; ++kb) {
+        const int g = kb_base + kb;
+        const int s = g % STAGES;
+        const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+        if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[s]), ph, kWaitLimitCycles)) {
+          atomicExch(&s_abort, 1);
+          break;
+        }
+        if (*(volatile int*)&s_abort) break;
+        ptx::tc_fence_after();
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t ah = ptx::sdesc_sw128(x_addr(s, 0) + kk * 32);
+          const uint64_t bh = ptx::sdesc_sw128(y_addr(s, 0) + kk * 32);
+          const uint32_t acc = (kb | kk) != 0;
+          if (PREC == NMF_TF32) {
+            ptx::mma_tf32(tmem, ah, bh, IDESC, acc);
+          } else {
+            ptx::mma_bf16(tmem, ah, bh, IDESC, acc);
+            if (X3) {
+              const uint64_t al = ptx::sdesc_sw128(x_addr(s, 1) + kk * 32);
+              const uint64_t bl = ptx::sdesc_sw128(y_addr(s, 1) + kk * 32);
+              ptx::mma_bf16(tmem, ah, bl, IDESC, 1);
+              ptx::mma_bf16(tmem, al, bh, IDESC, 1);
+            }
           }
         }
+        ptx::mma_commit(ptx::smem_u32(&empty_bar[s]));
       }
-      ptx::mma_commit(ptx::smem_u32(&empty_bar[s]));
+      // Always signal: also covers MMAs still in flight on the abort path.
+      ptx::mma_commit(ptx::smem_u32(&acc_bar));
     }
-    // Always signal: also covers MMAs still in flight on the abort path.
-    ptx::mma_commit(ptx::smem_u32(&acc_bar));
-  }
-  __syncwarp();
+    __syncwarp();
+    kb_base += nkb_run;
 
-  // ---------------- accumulator -> registers ----------------
-  const bool acc_ok = ptx::mbar_wait(ptx::smem_u32(&acc_bar), 0, kWaitLimitNs);
-  ptx::tc_fence_after();
-  if (!acc_ok) atomicExch(&s_abort, 1);
-  __syncthreads();
-  const bool abort = *(volatile int*)&s_abort != 0;
+    // ---------------- accumulator -> shared memory ----------------
+    const bool acc_ok = ptx::mbar_wait(ptx::smem_u32(&acc_bar), (uint32_t)it & 1u, kWaitLimitCycles);
+    ptx::tc_fence_after();
+    if (!acc_ok) atomicExch(&s_abort, 1);
+    __syncthreads();
+    const bool abort = *(volatile int*)&s_abort != 0;
 
-  constexpr int LD = RPAD + 1;
-  float* Ns = reinterpret_cast<float*>(smem);
-  float* Os = Ns + kBM * LD;
-  float* Gs = Os + kBM * LD;
-  const int row = warp * 32 + lane;  // TMEM lane == tile row
-  if (!abort) {
-    float* part = a.part + ((int64_t)tile * a.splits + split) * RPAD * kBM;
+    float* Acc = reinterpret_cast<float*>(smem);                       // [128][LDA]  (S > 1)
+    float* Ns = S > 1 ? reinterpret_cast<float*>(smem + Sh::ACC) : Acc; // [R][LD]
+    const int R = kBM / S;
+    float* Os = Ns + R * LD;
+    float* Gs = Os + R * LD;
+    const int row = warp * 32 + lane;  // TMEM lane == tile row
+    if (!abort) {
 #pragma unroll
-    for (int c = 0; c < RPAD / 16; ++c) {
-      float v[16];
-      ptx::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), v);
-      if (a.splits == 1) {
+      for (int c = 0; c < RPAD / 16; ++c) {
+        float v[16];
+        if (nkb_run > 0) {
+          ptx::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), v);
+        } else {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) Ns[row * LD + c * 16 + j] = v[j];
-      } else {
+          for (int j = 0; j < 16; ++j) v[j] = 0.f;
+        }
+        if (S == 1) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) part[(c * 16 + j) * kBM + row] = v[j];
+          for (int j = 0; j < 16; ++j) Ns[row * LD + c * 16 + j] = v[j];
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4)
+            *reinterpret_cast<float4*>(&Acc[row * LDA + c * 16 + j]) =
+                make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
       }
     }
+    ptx::tc_fence_before();
+    // Cluster barriers are executed the same number of times by every block
+    // of a cluster, aborted or not, so no block can wait on a peer forever.
+    if (S > 1) {
+      cluster.sync();   // every block's partial tile is in its shared memory
+      if (!abort) {
+        // rows [q R, (q+1) R) of the tile: sum the S partial tiles in rank order
+        for (int i = threadIdx.x; i < R * (RPAD / 4); i += kThreads) {
+          const int m = i / (RPAD / 4), k4 = (i % (RPAD / 4)) * 4;
+          const float4* mine = reinterpret_cast<const float4*>(&Acc[(q * R + m) * LDA + k4]);
+          float4 v[8];
+#pragma unroll
+          for (int s = 0; s < 8; ++s)
+            if (s < S) v[s] = *cluster.map_shared_rank(mine, s);   // all loads first
+          float4 sum = v[0];
+#pragma unroll
+          for (int s = 1; s < 8; ++s)
+            if (s < S) { sum.x += v[s].x; sum.y += v[s].y; sum.z += v[s].z; sum.w += v[s].w; }
+          Ns[m * LD + k4 + 0] = sum.x; Ns[m * LD + k4 + 1] = sum.y;
+          Ns[m * LD + k4 + 2] = sum.z; Ns[m * LD + k4 + 3] = sum.w;
+        }
+      }
+      cluster.sync();   // peers are done reading this block's tile
+    } else {
+      __syncthreads();
+    }
+
+    if (!abort && !gram_ready) {
+      // wait until every block has published its share of the Gram
+      if (threadIdx.x == 0) {
+        const uint64_t t0 = ptx::globaltimer();
+        while (ld_acquire(a.gctr) < a.gtarget) {
+          if (ptx::globaltimer() - t0 > kWaitLimitNs) { atomicExch(&s_abort, 1); break; }
+        }
+      }
+      __syncthreads();
+      gram_ready = true;
+    }
+    if (!*(volatile int*)&s_abort) {
+      float* P = a.ep.gram_part + ((int64_t)tile * S + q) * a.r * a.r;
+      mu_epilogue<RPAD, kThreads>(Ns, Os, Gs, R, m0 + (int64_t)q * R, P, a.ep);
+    }
+    // The next tile's copies overwrite this shared memory through the async proxy.
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
   }
+
   ptx::tc_fence_before();
   __syncthreads();
-  if (warp == 1) ptx::tmem_dealloc(tmem, S::TMEM_COLS);
-  if (abort) {
-    if (threadIdx.x == 0) atomicExch(a.err, (int)NMF_ETIMEOUT);
-    return;
-  }
-
-  if (a.splits > 1) {
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const unsigned prev = atomicAdd(&a.counters[tile], 1u);
-      s_last = (prev == (unsigned)a.splits - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    const float* base = a.part + (int64_t)tile * a.splits * RPAD * kBM;
-    for (int i = threadIdx.x; i < RPAD * kBM; i += kThreads) {
-      float sum = 0.f;
-      for (int sp = 0; sp < a.splits; ++sp) sum += __ldcg(base + (int64_t)sp * RPAD * kBM + i);
-      Ns[(i % kBM) * LD + (i / kBM)] = sum;
-    }
-    if (threadIdx.x == 0) a.counters[tile] = 0u;
-  }
-  __syncthreads();
-  mu_epilogue<kBM, RPAD, kThreads>(Ns, Os, Gs, m0, tile, a.ep);
+  if (warp == 1) ptx::tmem_dealloc(tmem, Sh::TMEM_COLS);
+  if (*(volatile int*)&s_abort && threadIdx.x == 0) atomicExch(a.err, (int)NMF_ETIMEOUT);
 }
 
 // ---------------------------------------------------------------------------
-// Host side: tensor maps and launch.
+// Host side: tensor maps, work plan and launch.
 // ---------------------------------------------------------------------------
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -284,35 +402,82 @@ bool make_map(CUtensorMap* map, const void* base, bool bf16, int64_t K, int64_t 
   return true;
 }
 
-template <int PREC, int RPAD>
-cudaError_t launch_t(const TcPlan& pl, const TcParams& prm, cudaStream_t st) {
-  using S = TcShape<PREC, RPAD>;
-  auto kern = k_stream_tc<PREC, RPAD>;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
+// 3-D map over a tile-blocked copy: blocks of 128 rows x 128 bytes stored
+// contiguously, `nblocks` of them; box = one block.
+bool make_map_blocked(CUtensorMap* map, const void* base, bool bf16, int64_t nblocks,
+                      std::string* err) {
+  EncodeTiled enc = get_encode();
+  if (!enc) { if (err) *err = "cuTensorMapEncodeTiled unavailable"; return false; }
+  const int esz = bf16 ? 2 : 4;
+  const int kbe = 128 / esz;
+  cuuint64_t dims[3] = {(cuuint64_t)kbe, 128, (cuuint64_t)nblocks};
+  cuuint64_t strides[2] = {128, 128 * 128};
+  cuuint32_t box[3] = {(cuuint32_t)kbe, 128, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                   3, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    if (err) *err = "cuTensorMapEncodeTiled (blocked) failed (code " + std::to_string((int)r) + ")";
+    return false;
   }
-  dim3 grid((unsigned)pl.tiles, (unsigned)pl.splits);
-  kern<<<grid, kThreads, S::SMEM, st>>>(pl.x_hi, pl.x_lo, pl.y_hi, pl.y_lo, prm);
-  return cudaGetLastError();
+  return true;
+}
+
+template <int PREC, int RPAD>
+void* kernel_ptr() {
+  return reinterpret_cast<void*>(k_stream_tc<PREC, RPAD>);
+}
+template <int PREC, int RPAD>
+int smem_bytes() {
+  return TcShape<PREC, RPAD>::SMEM;
 }
 
 template <int PREC>
-cudaError_t launch_prec(const TcPlan& pl, const TcParams& prm, cudaStream_t st) {
-  switch (pl.rpad) {
-    case 16: return launch_t<PREC, 16>(pl, prm, st);
-    case 32: return launch_t<PREC, 32>(pl, prm, st);
-    case 48: return launch_t<PREC, 48>(pl, prm, st);
-    case 64: return launch_t<PREC, 64>(pl, prm, st);
-    case 80: return launch_t<PREC, 80>(pl, prm, st);
-    case 96: return launch_t<PREC, 96>(pl, prm, st);
-    case 112: return launch_t<PREC, 112>(pl, prm, st);
-    case 128: return launch_t<PREC, 128>(pl, prm, st);
+bool kernel_info(int rpad, void** fn, int* smem) {
+  switch (rpad) {
+#define NMF_CASE(R) case R: *fn = kernel_ptr<PREC, R>(); *smem = smem_bytes<PREC, R>(); return true;
+    NMF_CASE(16) NMF_CASE(32) NMF_CASE(48) NMF_CASE(64)
+    NMF_CASE(80) NMF_CASE(96) NMF_CASE(112) NMF_CASE(128)
+#undef NMF_CASE
   }
-  return cudaErrorInvalidValue;
+  return false;
+}
+
+bool kernel_for(int prec, int rpad, void** fn, int* smem) {
+  switch (prec) {
+    case NMF_TF32: return kernel_info<NMF_TF32>(rpad, fn, smem);
+    case NMF_BF16X3: return kernel_info<NMF_BF16X3>(rpad, fn, smem);
+    case NMF_BF16: return kernel_info<NMF_BF16>(rpad, fn, smem);
+  }
+  return false;
+}
+
+cudaError_t prepare_kernel(void* fn, int smem) {
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+int max_clusters(void* fn, int smem, int S, int sms) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((sms / S) * S), 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = (unsigned)S;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 }  // namespace
@@ -327,25 +492,63 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
   pl.kblock = (prec == NMF_TF32) ? 32 : 64;
   pl.M = M; pl.K = K; pl.r = r;
   pl.tiles = (int)ceil_div(M, kBM);
-  const int64_t nkb = ceil_div(K, pl.kblock);
-  int splits;
-  if (user_split > 0) {
-    splits = user_split;
-  } else {
-    // About 4 waves of one block per SM, at least 4 k-blocks per split.
-    splits = (int)ceil_div((int64_t)sms * 4, pl.tiles);
-    const int64_t max_by_k = ceil_div(nkb, 4);
-    if (splits > max_by_k) splits = (int)max_by_k;
-    if (splits < 1) splits = 1;
-  }
-  pl.kchunk = ceil_div(nkb, splits) * pl.kblock;
-  pl.splits = (int)ceil_div(K, pl.kchunk);
-  const bool bf = prec != NMF_TF32;
   if (M > INT32_MAX || K > INT32_MAX) { if (err) *err = "size exceeds TMA coordinates"; return NMF_EINVAL; }
-  if (!make_map(&pl.x_hi, X_hi, bf, K, M, ldx, kBM, err)) return NMF_ECUDA;
+  void* fn = nullptr;
+  int smem = 0;
+  if (!kernel_for(prec, pl.rpad, &fn, &smem)) { if (err) *err = "no kernel for this rank"; return NMF_EINVAL; }
+  if (prepare_kernel(fn, smem) != cudaSuccess) {
+    (void)cudaGetLastError();
+    if (err) *err = "cannot configure the tensor-core kernel's shared memory";
+    return NMF_ECUDA;
+  }
+  pl.smem = smem;
+  const int64_t nkb = ceil_div(K, pl.kblock);
+  // Choose the cluster size S: fewest rounds of K/S work per block, then the
+  // most blocks at work.
+  int bestS = 0, bestG = 0;
+  double best_cost = 1e300;
+  int want = user_split;
+  if (want > 0) {
+    if (want != 1 && want != 2 && want != 4 && want != 8) {
+      if (err) *err = "split_k must be 1, 2, 4 or 8 for tensor-core precisions";
+      return NMF_EINVAL;
+    }
+    while (want > 1 && nkb < (int64_t)want) want /= 2;   // at most one split per k-block
+  }
+  for (int S = 1; S <= 8; S *= 2) {
+    if (want > 0 && S != want) continue;
+    if (S > 1 && nkb < (int64_t)S) continue;
+    const int maxc = max_clusters(fn, smem, S, sms);
+    if (maxc < 1) continue;
+    const int G = maxc < pl.tiles ? maxc : pl.tiles;
+    const int rounds = (int)ceil_div(pl.tiles, G);
+    const double cost = (double)rounds * (double)ceil_div(nkb, S) + 0.25 * rounds;
+    if (cost < best_cost - 1e-9 || (cost < best_cost + 1e-9 && G * S > bestG * bestS)) {
+      best_cost = cost;
+      bestS = S;
+      bestG = G;
+    }
+  }
+  if (bestS == 0) {
+    if (err) *err = user_split > 0 ? "split_k must be 1, 2, 4 or 8 for tensor-core precisions "
+                                     "(and at most the number of k-blocks)"
+                                   : "no co-resident cluster configuration";
+    return user_split > 0 ? NMF_EINVAL : NMF_EUNSUPPORTED;
+  }
+  pl.S = bestS;
+  pl.nclusters = bestG;
+  pl.splits = bestS;
+  pl.kchunk = ceil_div(nkb, bestS) * pl.kblock;
+  pl.grid = bestG * bestS;
+  pl.fn = fn;
+  const bool bf = prec != NMF_TF32;
+  (void)ldx;
+  pl.nkbt = (int)nkb;
+  const int64_t nblocks = (int64_t)pl.tiles * nkb;
+  if (!make_map_blocked(&pl.x_hi, X_hi, bf, nblocks, err)) return NMF_ECUDA;
   if (!make_map(&pl.y_hi, Y_hi, bf, K, r, ldy, pl.rpad, err)) return NMF_ECUDA;
   if (prec == NMF_BF16X3) {
-    if (!make_map(&pl.x_lo, X_lo, bf, K, M, ldx, kBM, err)) return NMF_ECUDA;
+    if (!make_map_blocked(&pl.x_lo, X_lo, bf, nblocks, err)) return NMF_ECUDA;
     if (!make_map(&pl.y_lo, Y_lo, bf, K, r, ldy, pl.rpad, err)) return NMF_ECUDA;
   } else {
     pl.x_lo = pl.x_hi;
@@ -354,15 +557,36 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
   return NMF_OK;
 }
 
-cudaError_t tc_launch(const TcPlan& pl, const SplitArgs& sp, const EpiArgs& ep, int* err,
+cudaError_t tc_launch(const TcPlan& pl, const EpiArgs& ep, const TcGram& gr, int* err,
                       cudaStream_t st) {
-  TcParams prm{pl.M, pl.K, pl.r, sp.splits, sp.kchunk, sp.part, sp.counters, ep, err};
-  switch (pl.prec) {
-    case NMF_TF32: return launch_prec<NMF_TF32>(pl, prm, st);
-    case NMF_BF16X3: return launch_prec<NMF_BF16X3>(pl, prm, st);
-    case NMF_BF16: return launch_prec<NMF_BF16>(pl, prm, st);
-  }
-  return cudaErrorInvalidValue;
+  TcParams prm;
+  prm.M = pl.M; prm.K = pl.K; prm.r = pl.r;
+  prm.S = pl.S; prm.tiles = pl.tiles; prm.nclusters = pl.nclusters; prm.kper = pl.kchunk;
+  prm.nkbt = pl.nkbt;
+  prm.ep = ep;
+  prm.gin = gr.gin; prm.gin_count = gr.gin_count;
+  prm.G32 = gr.G32; prm.G64 = gr.G64;
+  prm.gctr = gr.ctr; prm.gtarget = gr.target;
+  prm.err = err;
+  prm.ep.G = gr.G32;
+
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)pl.grid, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)pl.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = (unsigned)pl.S;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  void* args[] = {(void*)&pl.x_hi, (void*)&pl.x_lo, (void*)&pl.y_hi, (void*)&pl.y_lo,
+                  (void*)&prm};
+  cudaError_t e = cudaLaunchKernelExC(&cfg, pl.fn, args);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
 }
 
 }  // namespace nmf

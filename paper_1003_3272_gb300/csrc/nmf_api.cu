@@ -56,6 +56,7 @@ struct HalfPlan {
   EpiArgs ep{};
   float* G32_out = nullptr;   // Gram of the updated factor (output of the reduce)
   double* G64_out = nullptr;
+  int own = 0;                // factor this half updates: 0 = W, 1 = H
   TcPlan tc{};                // tcgen05 launch plan (tensor-core precisions)
 };
 
@@ -84,7 +85,12 @@ struct nmf_ctx {
   // Grams
   float* GW32 = nullptr; double* GW64 = nullptr;
   float* GH32 = nullptr; double* GH64 = nullptr;
-  float* gram_part = nullptr;
+  // per-factor partial Grams ([count][r][r]) left by the last producer of
+  // that factor; the matching Gram is their float64 sum.
+  float* gpart[2] = {nullptr, nullptr};   // [0] W, [1] H
+  int gcount[2] = {0, 0};
+  unsigned long long* gctr = nullptr;     // grid-wide counter of the tensor-core kernel
+  unsigned long long gctr_host = 0;       // its value after every launch so far
   // split-K
   float* part = nullptr;
   unsigned* counters = nullptr;
@@ -225,19 +231,21 @@ nmf_status prepare(nmf_ctx* c, bool seed_factors, uint64_t seed) {
   const int r = c->r;
   cudaStream_t st = c->st;
   ProfScope ps(c, 3);
-  if (c->plane == kPlaneF32 || c->plane == kPlaneTF32) {
-    const bool t32 = c->plane == kPlaneTF32;
+  if (c->plane == kPlaneF32) {
     if (c->Xw_hi != c->V) {
-      CK(launch_copy_pad(c->V, p, n, n, (float*)c->Xw_hi, c->ld_n, t32, st), "copy V");
+      CK(launch_copy_pad(c->V, p, n, n, (float*)c->Xw_hi, c->ld_n, false, st), "copy V");
       launched(1);
     }
-    CK(launch_transpose_pad(c->V, p, n, n, (float*)c->Xh_hi, c->ld_p, t32, st), "transpose V");
+    CK(launch_transpose_pad(c->V, p, n, n, (float*)c->Xh_hi, c->ld_p, false, st), "transpose V");
     launched(1);
   } else {
-    CK(launch_split_bf16(c->V, p, n, n, false, (__nv_bfloat16*)c->Xw_hi, (__nv_bfloat16*)c->Xw_lo,
-                         c->ld_n, st), "split V");
-    CK(launch_split_bf16(c->V, p, n, n, true, (__nv_bfloat16*)c->Xh_hi, (__nv_bfloat16*)c->Xh_lo,
-                         c->ld_p, st), "split V^T");
+    // tile-blocked copies: Xw = V (p x n), Xh = V^T (n x p)
+    const bool t32 = c->plane == kPlaneTF32;
+    const int kbe = t32 ? 32 : 64;
+    CK(launch_operand_blocked(c->V, p, n, n, false, t32, (void*)c->Xw_hi, (void*)c->Xw_lo,
+                              ceil_div(n, kbe), kbe, st), "operand V");
+    CK(launch_operand_blocked(c->V, p, n, n, true, t32, (void*)c->Xh_hi, (void*)c->Xh_lo,
+                              ceil_div(p, kbe), kbe, st), "operand V^T");
     launched(2);
   }
   if (seed_factors) {
@@ -249,12 +257,12 @@ nmf_status prepare(nmf_ctx* c, bool seed_factors, uint64_t seed) {
                           c->plane, st), "W planes");
   CK(launch_factor_planes(c->H, kFactorColMajor, n, n, r, c->Hop_hi, c->Hop_lo, c->ld_n,
                           c->plane, st), "H planes");
-  CK(launch_gram_tiles(c->W, kFactorRowMajor, p, r, r, c->gram_part, 128, st), "gram W");
-  CK(launch_gram_reduce(c->gram_part, (int)ceil_div(p, 128), r, c->GW32, c->GW64, st),
-     "gram W reduce");
-  CK(launch_gram_tiles(c->H, kFactorColMajor, n, n, r, c->gram_part, 128, st), "gram H");
-  CK(launch_gram_reduce(c->gram_part, (int)ceil_div(n, 128), r, c->GH32, c->GH64, st),
-     "gram H reduce");
+  CK(launch_gram_tiles(c->W, kFactorRowMajor, p, r, r, c->gpart[0], 128, st), "gram W");
+  c->gcount[0] = (int)ceil_div(p, 128);
+  CK(launch_gram_reduce(c->gpart[0], c->gcount[0], r, c->GW32, c->GW64, st), "gram W reduce");
+  CK(launch_gram_tiles(c->H, kFactorColMajor, n, n, r, c->gpart[1], 128, st), "gram H");
+  c->gcount[1] = (int)ceil_div(n, 128);
+  CK(launch_gram_reduce(c->gpart[1], c->gcount[1], r, c->GH32, c->GH64, st), "gram H reduce");
   launched(6);
   return NMF_OK;
 }
@@ -300,8 +308,8 @@ nmf_status build_ctx(nmf_ctx* c) {
   c->plane = (prec == NMF_BF16X3) ? kPlaneBF16x2
              : (prec == NMF_BF16) ? kPlaneBF16 : (prec == NMF_TF32 ? kPlaneTF32 : kPlaneF32);
   c->rpad = tc ? rank_pad16(r) : (int)round_up(r, 8);
-  if (!bf) {
-    if (prec == NMF_FP32 && n == c->ld_n && is_aligned16(c->V)) {
+  if (prec == NMF_FP32) {
+    if (n == c->ld_n && is_aligned16(c->V)) {
       c->Xw_hi = c->V;
     } else {
       float* d;
@@ -312,13 +320,16 @@ nmf_status build_ctx(nmf_ctx* c) {
     if ((s = dalloc(c, (void**)&t, (size_t)n * c->ld_p * 4)) != NMF_OK) return s;
     c->Xh_hi = t;
   } else {
-    const bool lo = prec == NMF_BF16X3;
-    __nv_bfloat16 *a = nullptr, *b = nullptr, *ta = nullptr, *tb = nullptr;
-    if ((s = dalloc(c, (void**)&a, (size_t)p * c->ld_n * 2)) != NMF_OK) return s;
-    if ((s = dalloc(c, (void**)&ta, (size_t)n * c->ld_p * 2)) != NMF_OK) return s;
-    if (lo) {
-      if ((s = dalloc(c, (void**)&b, (size_t)p * c->ld_n * 2)) != NMF_OK) return s;
-      if ((s = dalloc(c, (void**)&tb, (size_t)n * c->ld_p * 2)) != NMF_OK) return s;
+    // tile-blocked copies (128 rows x 128 bytes per block), zero padded
+    const int kbe = prec == NMF_TF32 ? 32 : 64;
+    const size_t bw = (size_t)ceil_div(p, 128) * ceil_div(n, kbe) * 128 * 128;  // bytes
+    const size_t bh = (size_t)ceil_div(n, 128) * ceil_div(p, kbe) * 128 * 128;
+    void *a = nullptr, *b = nullptr, *ta = nullptr, *tb = nullptr;
+    if ((s = dalloc(c, &a, bw)) != NMF_OK) return s;
+    if ((s = dalloc(c, &ta, bh)) != NMF_OK) return s;
+    if (prec == NMF_BF16X3) {
+      if ((s = dalloc(c, &b, bw)) != NMF_OK) return s;
+      if ((s = dalloc(c, &tb, bh)) != NMF_OK) return s;
     }
     c->Xw_hi = a; c->Xw_lo = b; c->Xh_hi = ta; c->Xh_lo = tb;
   }
@@ -353,12 +364,13 @@ nmf_status build_ctx(nmf_ctx* c) {
 
   hh.ep.F = c->H; hh.ep.ldf = n; hh.ep.layout = kFactorColMajor; hh.ep.M = n;
   hh.ep.op_hi = c->Hop_hi; hh.ep.op_lo = c->Hop_lo; hh.ep.ldop = c->ld_n;
-  hh.ep.G = c->GW32; hh.G32_out = c->GH32; hh.G64_out = c->GH64;
+  hh.ep.G = c->GW32; hh.G32_out = c->GH32; hh.G64_out = c->GH64; hh.own = 1;
   hw.ep.F = c->W; hw.ep.ldf = r; hw.ep.layout = kFactorRowMajor; hw.ep.M = p;
   hw.ep.op_hi = c->Wop_hi; hw.ep.op_lo = c->Wop_lo; hw.ep.ldop = c->ld_p;
-  hw.ep.G = c->GH32; hw.G32_out = c->GW32; hw.G64_out = c->GW64;
+  hw.ep.G = c->GH32; hw.G32_out = c->GW32; hw.G64_out = c->GW64; hw.own = 0;
 
-  size_t part_floats = 0, counters = 0, gram_tiles = 0;
+  size_t part_floats = 0, counters = 0;
+  size_t gtiles[2] = {(size_t)ceil_div(p, 128), (size_t)ceil_div(n, 128)};
   for (HalfPlan* h : {&hh, &hw}) {
     h->ep.r = r;
     h->ep.eps = c->cfg.eps;
@@ -376,19 +388,23 @@ nmf_status build_ctx(nmf_ctx* c) {
       h->splits = h->tc.splits;
       h->kchunk = h->tc.kchunk;
     }
-    const int rp_acc = tc ? c->rpad : (int)round_up(r, 8);
-    if (h->splits > 1) {
-      const size_t pf = (size_t)h->tiles * h->splits * bm * rp_acc;
+    if (!tc && h->splits > 1) {
+      const size_t pf = (size_t)h->tiles * h->splits * bm * round_up(r, 8);
       if (pf > part_floats) part_floats = pf;
     }
     if ((size_t)h->tiles > counters) counters = h->tiles;
-    const size_t gt = ceil_div(h->M, 128) > h->tiles ? ceil_div(h->M, 128) : h->tiles;
-    if (gt > gram_tiles) gram_tiles = gt;
+    // partial Grams this half produces: one per tile (fp32 form) or per
+    // tile row slice (tensor-core form)
+    const size_t np = tc ? (size_t)h->tiles * h->tc.S : (size_t)h->tiles;
+    if (np > gtiles[h->own]) gtiles[h->own] = np;
   }
   if ((s = dalloc(c, (void**)&c->part, part_floats * 4)) != NMF_OK) return s;
   if ((s = dalloc(c, (void**)&c->counters, counters * 4)) != NMF_OK) return s;
-  if ((s = dalloc(c, (void**)&c->gram_part, gram_tiles * rr * 4)) != NMF_OK) return s;
-  for (HalfPlan* h : {&hh, &hw}) h->ep.gram_part = c->gram_part;
+  for (int f = 0; f < 2; ++f)
+    if ((s = dalloc(c, (void**)&c->gpart[f], gtiles[f] * rr * 4)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->gctr, sizeof(unsigned long long))) != NMF_OK) return s;
+  c->gctr_host = 0;
+  for (HalfPlan* h : {&hh, &hw}) h->ep.gram_part = c->gpart[h->own];
   if ((s = dalloc(c, (void**)&c->obj_parts, objective_parts() * 8)) != NMF_OK) return s;
   if ((s = dalloc(c, (void**)&c->f_dev, 8)) != NMF_OK) return s;
   if ((s = dalloc(c, (void**)&c->err_dev, sizeof(int))) != NMF_OK) return s;
@@ -427,21 +443,44 @@ nmf_status check_device_error(nmf_ctx* c) {
 
 nmf_status run_half(nmf_ctx* c, int which) {
   HalfPlan& h = c->half[which];
-  SplitArgs sp{c->part, c->counters, h.splits, h.kchunk};
-  {
-  ProfScope ps(c, 0);
+  const int own = h.own, other = 1 - h.own;
   if (c->cfg.prec == NMF_FP32) {
-    CK(launch_stream_simt(static_cast<const float*>(h.X_hi), h.ldx,
-                          static_cast<const float*>(h.Y_hi), h.ldy, h.M, h.K, c->r, sp, h.ep,
-                          c->st), "stream (fp32)");
+    SplitArgs sp{c->part, c->counters, h.splits, h.kchunk};
+    {
+      ProfScope ps(c, 0);
+      CK(launch_stream_simt(static_cast<const float*>(h.X_hi), h.ldx,
+                            static_cast<const float*>(h.Y_hi), h.ldy, h.M, h.K, c->r, sp, h.ep,
+                            c->st), "stream (fp32)");
+      launched(1);
+    }
+    c->gcount[own] = h.tiles;
+    ProfScope ps(c, 1);
+    CK(launch_gram_reduce(c->gpart[own], c->gcount[own], c->r, h.G32_out, h.G64_out, c->st),
+       "gram reduce");
+    launched(1);
   } else {
-    CK(tc_launch(h.tc, sp, h.ep, c->err_dev, c->st), "stream (tensor)");
+    // The launch first reduces the other factor's partial Grams (left by the
+    // previous half step or by the start), then streams V and updates.
+    TcGram g;
+    g.gin = c->gpart[other];
+    g.gin_count = c->gcount[other];
+    g.G32 = other == 0 ? c->GW32 : c->GH32;
+    g.G64 = other == 0 ? c->GW64 : c->GH64;
+    g.ctr = c->gctr;
+    c->gctr_host += (unsigned long long)h.tc.grid;
+    g.target = c->gctr_host;
+    ProfScope ps(c, 0);
+    CK(tc_launch(h.tc, h.ep, g, c->err_dev, c->st), "stream (tensor)");
+    launched(1);
+    c->gcount[own] = h.tiles * h.tc.S;
   }
-  launched(1);
-  }
-  ProfScope ps(c, 1);
-  CK(launch_gram_reduce(c->gram_part, h.tiles, c->r, h.G32_out, h.G64_out, c->st),
-     "gram reduce");
+  return NMF_OK;
+}
+
+// Float64 Gram of factor f (0 = W, 1 = H) from its current partials.
+nmf_status reduce_gram(nmf_ctx* c, int f) {
+  CK(launch_gram_reduce(c->gpart[f], c->gcount[f], c->r, f == 0 ? c->GW32 : c->GH32,
+                        f == 0 ? c->GW64 : c->GH64, c->st), "gram reduce");
   launched(1);
   return NMF_OK;
 }
@@ -549,6 +588,8 @@ nmf_status nmf_read_gram(nmf_ctx* c, int which, double* out) {
     set_err(c ? &c->err : nullptr, "bad argument to nmf_read_gram");
     return NMF_EINVAL;
   }
+  nmf_status s = reduce_gram(c, which);
+  if (s != NMF_OK) return s;
   CK(cudaMemcpyAsync(out, which == 0 ? c->GW64 : c->GH64, (size_t)c->r * c->r * 8,
                      cudaMemcpyDeviceToHost, c->st), "memcpy gram");
   return check_device_error(c);

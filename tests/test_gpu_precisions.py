@@ -91,12 +91,33 @@ def test_deterministic(prec):
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
-@pytest.mark.parametrize("split_k", [1, 2, 5])
-def test_split_variants(prec, split_k):
+@pytest.mark.parametrize("split_k", [1, 2, 4, 8])
+def test_cluster_split_variants(prec, split_k):
+    """Every cluster size (K-splits per tile) gives the same answer within the
+    precision's bar; results are deterministic for a given split."""
     pr = synth.uniform_problem(300, 1100, 24, seed=12)
     Wg, Hg, fg = run_gpu(pr.V, pr.W0, pr.H0, 3, prec=prec, split_k=split_k)
     Wo, Ho, fo = oracle_run(pr.V, pr.W0, pr.H0, 3)
     assert abs(fg - fo) / fo <= ITER_OBJ_BAR[prec]
+    assert entry_rel_err(Wg, Wo)[1] <= ITER_ENTRY_BAR[prec]
+
+
+def test_invalid_cluster_split_is_rejected():
+    from paper_1003_3272_gb300 import nmf
+    pr = synth.uniform_problem(300, 1100, 24, seed=12)
+    with pytest.raises(nmf.NMFError) as ei:
+        nmf.NMF(to_dev(pr.V), to_dev(pr.W0), to_dev(pr.H0), prec="bf16x3", split_k=5)
+    assert ei.value.status == nmf.EINVAL
+
+
+def test_many_tiles_persistent_loop():
+    """More row tiles than co-resident clusters: the persistent grid walks
+    several tiles per cluster (tall V)."""
+    pr = synth.uniform_problem(40000, 300, 16, seed=21)
+    Wg, Hg, fg = run_gpu(pr.V, pr.W0, pr.H0, 2, prec="bf16x3")
+    Wo, Ho, fo = oracle_run(pr.V, pr.W0, pr.H0, 2)
+    assert entry_rel_err(Wg, Wo)[0] <= 1e-3
+    assert abs(fg - fo) / fo <= 1e-5
 
 
 def test_exact_planted_fixed_point_bf16x3():
