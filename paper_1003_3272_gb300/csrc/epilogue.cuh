@@ -20,10 +20,16 @@
 
 namespace nmf {
 
+// Row strides of the epilogue's shared tiles: Ns (numerator, then new
+// factor) keeps 16-byte aligned rows for the Gram's vector loads; Os (old
+// factor) uses an odd stride so that column reads are bank-conflict free.
+template <int RPAD> __host__ __device__ constexpr int epi_ldn() { return RPAD + 4; }
+template <int RPAD> __host__ __device__ constexpr int epi_ldo() { return RPAD + 1; }
+
 // Shared-memory floats needed by mu_epilogue for an R x RPAD slice.
 template <int RPAD>
 __host__ __device__ constexpr int epi_smem_floats(int R) {
-  return 2 * R * (RPAD + 1) + RPAD * RPAD;
+  return R * epi_ldn<RPAD>() + R * epi_ldo<RPAD>() + RPAD * RPAD;
 }
 
 __device__ __forceinline__ void store_plane(const EpiArgs& e, int k, int64_t m, float v) {
@@ -44,17 +50,21 @@ __device__ __forceinline__ void store_plane(const EpiArgs& e, int k, int64_t m, 
 
 // Multiply-divide update of an R-row slice of a tile whose first row is
 // global row `row0` (rows beyond e.M are ignored).
-// Ns: [R][RPAD+1] holds the final numerator slice on entry and the new
+// Ns: [R][RPAD+4] holds the final numerator slice on entry and the new
 //     factor slice on exit.
 // Os: [R][RPAD+1] scratch for the old factor slice.
 // Gs: [RPAD][RPAD] scratch, filled here from e.G (the other factor's Gram,
 //     read through L2: it may have been written earlier in the same launch).
 // P : r x r destination of the slice's partial Gram of the new factor.
+// Both products in here -- the denominators old . G and the partial Gram
+// new^T new -- are register-blocked so that each thread keeps 16-32
+// independent accumulators (the block has few warps to hide latency with).
 // All NT threads of the block must call it.
 template <int RPAD, int NT>
 __device__ void mu_epilogue(float* Ns, float* Os, float* Gs, int R, int64_t row0, float* P,
                             const EpiArgs& e) {
-  constexpr int LD = RPAD + 1;
+  constexpr int LDN = epi_ldn<RPAD>();
+  constexpr int LDO = epi_ldo<RPAD>();
   const int tid = threadIdx.x;
   const int r = e.r;
   const int64_t M = e.M;
@@ -86,7 +96,7 @@ __device__ void mu_epilogue(float* Ns, float* Os, float* Gs, int R, int64_t row0
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int i = b + j * NT;
-        if (i < R * RPAD) Os[(i / RPAD) * LD + (i % RPAD)] = v[j];
+        if (i < R * RPAD) Os[(i / RPAD) * LDO + (i % RPAD)] = v[j];
       }
     }
   } else {
@@ -101,37 +111,55 @@ __device__ void mu_epilogue(float* Ns, float* Os, float* Gs, int R, int64_t row0
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int i = b + j * NT;
-        if (i < R * RPAD) Os[(i % R) * LD + (i / R)] = v[j];
+        if (i < R * RPAD) Os[(i % R) * LDO + (i / R)] = v[j];
       }
     }
   }
   __syncthreads();
 
-  // new = old * num / (old . G[:, k] + eps), eight ranks per work item.
-  constexpr int KG = RPAD / 8;
-  for (int it = tid; it < R * KG; it += NT) {
-    const int m = it % R, kg = it / R;
-    float den[8];
+  // ---- den = old . G + eps; new = old * num / den ---------------------------
+  // Thread (kg, mg): ranks kg*8 .. kg*8+7, rows mg, mg + MG, ... (4 at a time).
+  {
+    constexpr int KG = RPAD / 8;
+    constexpr int MG = NT / KG;
+    const int kg = tid % KG, mg = tid / KG;
+    for (int mb = mg; mb < R && tid < KG * MG; mb += 4 * MG) {
+      float acc[4][8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) den[j] = 0.f;
-    for (int l = 0; l < r; ++l) {
-      const float o = Os[m * LD + l];
-      const float4 g0 = *reinterpret_cast<const float4*>(&Gs[l * RPAD + kg * 8]);
-      const float4 g1 = *reinterpret_cast<const float4*>(&Gs[l * RPAD + kg * 8 + 4]);
-      den[0] = fmaf(o, g0.x, den[0]); den[1] = fmaf(o, g0.y, den[1]);
-      den[2] = fmaf(o, g0.z, den[2]); den[3] = fmaf(o, g0.w, den[3]);
-      den[4] = fmaf(o, g1.x, den[4]); den[5] = fmaf(o, g1.y, den[5]);
-      den[6] = fmaf(o, g1.z, den[6]); den[7] = fmaf(o, g1.w, den[7]);
-    }
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int k = kg * 8 + j;
-      float v = 0.f;
-      if (m < rows && k < r) {
-        const float d = __fadd_rn(den[j], e.eps);
-        v = __fdiv_rn(__fmul_rn(Os[m * LD + k], Ns[m * LD + k]), d);
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+      int mrow[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) mrow[i] = min(mb + i * MG, R - 1);
+#pragma unroll 2
+      for (int l = 0; l < r; ++l) {
+        const float4 g0 = *reinterpret_cast<const float4*>(&Gs[l * RPAD + kg * 8]);
+        const float4 g1 = *reinterpret_cast<const float4*>(&Gs[l * RPAD + kg * 8 + 4]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float o = Os[mrow[i] * LDO + l];
+          acc[i][0] = fmaf(o, g0.x, acc[i][0]); acc[i][1] = fmaf(o, g0.y, acc[i][1]);
+          acc[i][2] = fmaf(o, g0.z, acc[i][2]); acc[i][3] = fmaf(o, g0.w, acc[i][3]);
+          acc[i][4] = fmaf(o, g1.x, acc[i][4]); acc[i][5] = fmaf(o, g1.y, acc[i][5]);
+          acc[i][6] = fmaf(o, g1.z, acc[i][6]); acc[i][7] = fmaf(o, g1.w, acc[i][7]);
+        }
       }
-      Ns[m * LD + k] = v;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int m = mb + i * MG;
+        if (m >= R) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int k = kg * 8 + j;
+          float v = 0.f;
+          if (m < rows && k < r) {
+            const float d = __fadd_rn(acc[i][j], e.eps);
+            v = __fdiv_rn(__fmul_rn(Os[m * LDO + k], Ns[m * LDN + k]), d);
+          }
+          Ns[m * LDN + k] = v;
+        }
+      }
     }
   }
   __syncthreads();
@@ -140,29 +168,58 @@ __device__ void mu_epilogue(float* Ns, float* Os, float* Gs, int R, int64_t row0
   if (e.layout == kFactorRowMajor) {
     for (int i = tid; i < rows * r; i += NT) {
       const int m = i / r, k = i % r;
-      e.F[(row0 + m) * r + k] = Ns[m * LD + k];
+      e.F[(row0 + m) * r + k] = Ns[m * LDN + k];
     }
   } else {
     for (int i = tid; i < rows * r; i += NT) {
       const int k = i / rows, m = i % rows;
-      e.F[(int64_t)k * e.ldf + row0 + m] = Ns[m * LD + k];
+      e.F[(int64_t)k * e.ldf + row0 + m] = Ns[m * LDN + k];
     }
   }
   for (int i = tid; i < rows * r; i += NT) {
     const int k = i / rows, m = i % rows;
-    store_plane(e, k, row0 + m, Ns[m * LD + k]);
+    store_plane(e, k, row0 + m, Ns[m * LDN + k]);
   }
 
-  // Partial Gram of the new slice: P[k][l] = sum_m new[m,k] new[m,l], k <= l.
-  const int npairs = r * (r + 1) / 2;
-  for (int it = tid; it < npairs; it += NT) {
-    int k = 0, rem = it;
-    while (rem >= r - k) { rem -= r - k; ++k; }
-    const int l = k + rem;
-    float s = 0.f;
-    for (int m = 0; m < rows; ++m) s = fmaf(Ns[m * LD + k], Ns[m * LD + l], s);
-    P[k * r + l] = s;
-    P[l * r + k] = s;
+  // ---- partial Gram of the new slice: P = new^T new (rows >= `rows` are 0) --
+  // 4 x 4 blocks (kb <= lb) of the r x r result, one or more per thread,
+  // rows summed in order 0..R-1.
+  {
+    constexpr int NB = RPAD / 4;
+    const int nbr = (r + 3) / 4;
+    const int npairs = nbr * (nbr + 1) / 2;
+    for (int it = tid; it < npairs; it += NT) {
+      int kb = 0, rem = it;
+      while (rem >= nbr - kb) { rem -= nbr - kb; ++kb; }
+      const int lb = kb + rem;
+      float acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
+      for (int m = 0; m < R; ++m) {
+        const float4 a = *reinterpret_cast<const float4*>(&Ns[m * LDN + kb * 4]);
+        const float4 b = *reinterpret_cast<const float4*>(&Ns[m * LDN + lb * 4]);
+        const float av[4] = {a.x, a.y, a.z, a.w};
+        const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      }
+      (void)NB;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int k = kb * 4 + i, l = lb * 4 + j;
+          if (k < r && l < r) {
+            P[k * r + l] = acc[i][j];
+            P[l * r + k] = acc[i][j];
+          }
+        }
+    }
   }
 }
 

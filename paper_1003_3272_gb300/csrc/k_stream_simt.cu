@@ -125,10 +125,10 @@ k_stream_simt(const SimtParams a) {
   __syncthreads();
 
   // Reuse the staging buffers for the epilogue tiles.
-  constexpr int LD = RPAD + 1;
+  constexpr int LD = epi_ldn<RPAD>();
   float* Ns = smem;
   float* Os = Ns + BM * LD;
-  float* Gs = Os + BM * LD;
+  float* Gs = Os + BM * epi_ldo<RPAD>();
 
   if (a.sp.splits == 1) {
 #pragma unroll

@@ -43,7 +43,7 @@ namespace cg = cooperative_groups;
 namespace nmf {
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;   // 8 warps; warps 0-3 own the 128 TMEM lanes
 constexpr int kBM = 128;
 constexpr uint64_t kWaitLimitNs = 1500ull * 1000 * 1000;      // 1.5 s (global timer)
 constexpr uint64_t kWaitLimitCycles = 3000ull * 1000 * 1000;  // ~1.5 s at 2 GHz
@@ -110,7 +110,8 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
   constexpr bool X3 = PREC == NMF_BF16X3;
   constexpr uint32_t IDESC = ptx::idesc(PrecTraits<PREC>::FMT, kBM, RPAD);
   constexpr int LDA = Sh::LDA;
-  constexpr int LD = RPAD + 1;
+  constexpr int LDN = epi_ldn<RPAD>();
+  constexpr int LDO = epi_ldo<RPAD>();
 
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
@@ -277,12 +278,12 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
     const bool abort = *(volatile int*)&s_abort != 0;
 
     float* Acc = reinterpret_cast<float*>(smem);                       // [128][LDA]  (S > 1)
-    float* Ns = S > 1 ? reinterpret_cast<float*>(smem + Sh::ACC) : Acc; // [R][LD]
+    float* Ns = S > 1 ? reinterpret_cast<float*>(smem + Sh::ACC) : Acc; // [R][LDN]
     const int R = kBM / S;
-    float* Os = Ns + R * LD;
-    float* Gs = Os + R * LD;
+    float* Os = Ns + R * LDN;
+    float* Gs = Os + R * LDO;
     const int row = warp * 32 + lane;  // TMEM lane == tile row
-    if (!abort) {
+    if (!abort && warp < 4) {
 #pragma unroll
       for (int c = 0; c < RPAD / 16; ++c) {
         float v[16];
@@ -294,7 +295,9 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
         }
         if (S == 1) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) Ns[row * LD + c * 16 + j] = v[j];
+          for (int j = 0; j < 16; j += 4)
+            *reinterpret_cast<float4*>(&Ns[row * LDN + c * 16 + j]) =
+                make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
         } else {
 #pragma unroll
           for (int j = 0; j < 16; j += 4)
@@ -321,8 +324,7 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
 #pragma unroll
           for (int s = 1; s < 8; ++s)
             if (s < S) { sum.x += v[s].x; sum.y += v[s].y; sum.z += v[s].z; sum.w += v[s].w; }
-          Ns[m * LD + k4 + 0] = sum.x; Ns[m * LD + k4 + 1] = sum.y;
-          Ns[m * LD + k4 + 2] = sum.z; Ns[m * LD + k4 + 3] = sum.w;
+          *reinterpret_cast<float4*>(&Ns[m * LDN + k4]) = sum;
         }
       }
       cluster.sync();   // peers are done reading this block's tile
