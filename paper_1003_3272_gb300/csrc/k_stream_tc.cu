@@ -36,6 +36,7 @@
 
 #include "epilogue.cuh"
 #include "tc.cuh"
+#include "tc_epi.cuh"
 #include "tc_ptx.cuh"
 
 namespace cg = cooperative_groups;
@@ -47,24 +48,27 @@ constexpr int kThreads = 256;   // 8 warps; warps 0-3 own the 128 TMEM lanes
 constexpr int kBM = 128;
 constexpr uint64_t kWaitLimitNs = 1500ull * 1000 * 1000;      // 1.5 s (global timer)
 constexpr uint64_t kWaitLimitCycles = 3000ull * 1000 * 1000;  // ~1.5 s at 2 GHz
-constexpr int kSmemBudget = 200 * 1024;
+constexpr int kSmemMax = 227 * 1024;
 
 struct TcParams {
   int64_t M, K;
   int r;
-  int S;                 // cluster size = K-splits per tile
+  int S;                 // cluster size = K-splits per tile (>= 2)
   int tiles;
   int nclusters;
   int64_t kper;          // K per split (multiple of the k-block)
   int nkbt;              // k-blocks per tile row (blocked X layout)
-  EpiArgs ep;            // ep.gram_part: this launch's slice partials [tiles*S][r][r]
-  // Gram of the other factor, reduced in the prologue
-  const float* gin;      // partials [gin_count][r][r]
-  int gin_count;
-  float* G32;            // r x r outputs (ep.G aliases G32)
-  double* G64;
-  unsigned long long* gctr;   // grid-wide publication counter
-  unsigned long long gtarget; // value meaning "every block of this launch published"
+  EpiArgs ep;            // the factor being updated and its planes
+  // the other factor Q, whose Gram the helpers form in the prologue
+  const float* Q;
+  int q_layout;          // 0: Q[m * ldq + k] (W);  1: Q[k * ldq + m] (H)
+  int64_t ldq;
+  int64_t QM;            // rows of Q (p for W, n for H)
+  double* gpart;         // [grid][r][r] per-block partial Grams (workspace)
+  float* Gpad;           // [RPAD][RPAD] float32 Gram, zero padded
+  double* G64;           // [r][r] float64 Gram
+  unsigned long long* ctr;     // grid-wide publication counter (monotone)
+  unsigned long long base;     // its value before this launch
   int* err;              // device error word
 };
 
@@ -81,22 +85,32 @@ struct TcShape {
   static constexpr int Y_BYTES = RPAD * 128;      // one plane of Y
   static constexpr int STAGE = XPL * (X_BYTES + Y_BYTES);
   static constexpr int LDA = RPAD + 4;            // accumulator tile row stride (floats)
-  static constexpr int ACC = kBM * LDA * 4;
-  // epilogue region: [Acc (S > 1)] [Ns | Os | Gs for up to 128 rows]
-  static constexpr int EPI1 = epi_smem_floats<RPAD>(kBM) * 4;           // S = 1
-  static constexpr int EPI2 = ACC + epi_smem_floats<RPAD>(kBM / 2) * 4; // S >= 2
-  static constexpr int EPI = EPI1 > EPI2 ? EPI1 : EPI2;
-  static constexpr int STAGES_RAW = kSmemBudget / STAGE;
-  static constexpr int STAGES = STAGES_RAW > 8 ? 8 : (STAGES_RAW < 2 ? 2 : STAGES_RAW);
-  static constexpr int MAIN = STAGES * STAGE;
-  static constexpr int SMEM = (MAIN > EPI ? MAIN : EPI) + 1024;   // + alignment slack
+  static constexpr int ACC = kBM * LDA * 4;       // partial accumulator tile
+  static constexpr int NSB = tcepi::kRmax * epi_ldn<RPAD>() * 4;   // reduced slice
+  static constexpr int DED = tcepi::dedicated_floats<RPAD>() * 4;  // helpers' region
+  static constexpr int STAGES_RAW = (kSmemMax - DED - 2048) / STAGE;
+  static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
+  static constexpr int RING = STAGES * STAGE;
+  static constexpr int MAIN = RING > ACC + NSB ? RING : ACC + NSB;  // Acc/Ns reuse the ring
+  static constexpr int SMEM = MAIN + DED + 1024;   // + alignment slack
   static constexpr int TMEM_COLS = RPAD <= 32 ? 32 : (RPAD <= 64 ? 64 : 128);
+  static_assert(STAGES >= 2, "pipeline needs two stages");
 };
 
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
+}
+
+// One helper thread waits (bounded) for the counter; false on timeout.
+__device__ __forceinline__ bool wait_counter(const unsigned long long* ctr,
+                                             unsigned long long target) {
+  const uint64_t t0 = ptx::globaltimer();
+  while (ld_acquire(ctr) < target) {
+    if (ptx::globaltimer() - t0 > kWaitLimitNs) return false;
+  }
+  return true;
 }
 
 template <int PREC, int RPAD>
@@ -111,7 +125,6 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
   constexpr uint32_t IDESC = ptx::idesc(PrecTraits<PREC>::FMT, kBM, RPAD);
   constexpr int LDA = Sh::LDA;
   constexpr int LDN = epi_ldn<RPAD>();
-  constexpr int LDO = epi_ldo<RPAD>();
 
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
@@ -128,6 +141,13 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = ptx::smem_u32(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool helper = threadIdx.x >= tcepi::kHelperBase;
+  const int h = threadIdx.x - tcepi::kHelperBase;
+
+  // helpers' dedicated region: Qs | Os; denominators in the helpers' registers
+  float* Qs = reinterpret_cast<float*>(smem + Sh::MAIN);
+  float* Os = Qs + tcepi::kQsRows * tcepi::ldq<RPAD>();
+  tcepi::DenTile<RPAD> den;
 
   auto x_addr = [&](int s, int plane) { return sbase + s * Sh::STAGE + plane * Sh::X_BYTES; };
   auto y_addr = [&](int s, int plane) {
@@ -159,54 +179,80 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
   const int64_t kbeg = (int64_t)q * a.kper;
   const int64_t kend = min(a.K, kbeg + a.kper);
   const int nkb = kbeg < kend ? (int)ceil_div(kend - kbeg, KB) : 0;
+  const int R = kBM / S;
 
-  // ---- prologue: this block's share of the other factor's Gram ------------
-  if (warp >= 2) {
-    // Four entries per warp at a time, each lane summing every 32nd partial
-    // (loads issued together), then a fixed shuffle tree per entry.
-    const int rr = a.r * a.r;
-    const int nblk = gridDim.x;
-    const int e0 = (int)((int64_t)blockIdx.x * rr / nblk);
-    const int e1 = (int)((int64_t)(blockIdx.x + 1) * rr / nblk);
-    for (int eb = e0 + 4 * (warp - 2); eb < e1; eb += 8) {
-      double s4[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int t = lane; t < a.gin_count; t += 32) {
-        float v[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          v[j] = (eb + j < e1) ? __ldcg(a.gin + (int64_t)t * rr + eb + j) : 0.f;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) s4[j] += (double)v[j];
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) s4[j] += __shfl_down_sync(0xffffffffu, s4[j], o);
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (eb + j < e1) {
-            a.G64[eb + j] = s4[j];
-            a.G32[eb + j] = (float)s4[j];
-          }
-      }
+  // ---- helpers, prologue: old rows of the first tile, then the Gram of the
+  // other factor (partials over an even share of its rows, grid barrier,
+  // this block's share of the entries, grid barrier) ------------------------
+  if (helper) {
+    const int G = gridDim.x;
+    ptx::pdl_wait();   // the factors of the previous half step are final
+    if (cid < a.tiles) {
+      const int64_t row0 = (int64_t)cid * kBM + (int64_t)q * R;
+      const int rows = (int)max((int64_t)0, min((int64_t)R, a.M - row0));
+      tcepi::load_old<RPAD>(Os, a.ep, R, row0, rows, h);
+    }
+    const int64_t q0 = (int64_t)blockIdx.x * a.QM / G;
+    const int64_t q1 = (int64_t)(blockIdx.x + 1) * a.QM / G;
+    tcepi::gram_rows<RPAD>(Qs, a.Q, a.q_layout, a.ldq, q0, q1, a.r,
+                           a.gpart + (int64_t)blockIdx.x * a.r * a.r, h);
+    __threadfence();
+    tcepi::helper_sync();
+    if (h == 0) atomicAdd(a.ctr, 1ull);
+    if (h == 0 && !wait_counter(a.ctr, a.base + (unsigned long long)G)) atomicExch(&s_abort, 1);
+    tcepi::helper_sync();
+    if (!*(volatile int*)&s_abort) {
+      const int rr = a.r * a.r;
+      const int e0 = (int)((int64_t)blockIdx.x * rr / G);
+      const int e1 = (int)((int64_t)(blockIdx.x + 1) * rr / G);
+      tcepi::gram_reduce_slice<RPAD>(a.gpart, G, a.r, e0, e1, a.G64, a.Gpad,
+                                     reinterpret_cast<double*>(Qs), h);
     }
     __threadfence();
-    asm volatile("bar.sync 1, 64;" ::: "memory");
-    if (threadIdx.x == 64) atomicAdd(a.gctr, 1ull);
+    tcepi::helper_sync();
+    if (h == 0) atomicAdd(a.ctr, 1ull);
+    if (h == 0 && !wait_counter(a.ctr, a.base + 2ull * (unsigned long long)G))
+      atomicExch(&s_abort, 1);
+    tcepi::helper_sync();
   }
 
   int it = 0;        // tiles processed by this block
   int kb_base = 0;   // k-blocks processed by this block (ring position)
-  bool gram_ready = false;
   for (int tile = cid; tile < a.tiles; tile += a.nclusters, ++it) {
     const int64_t m0 = (int64_t)tile * kBM;
+    const int64_t row0 = m0 + (int64_t)q * R;
+    const int rows = (int)max((int64_t)0, min((int64_t)R, a.M - row0));
     const int nkb_run = *(volatile int*)&s_abort ? 0 : nkb;
     if (warp == 0 && lane == 0) {
       // ---------------- TMA producer ----------------
+      // First tile: the X halves of the first stages go out before waiting
+      // for the previous launch (V never changes); the Y halves (the factor
+      // the previous launch wrote) after.
       int issued = 0;
-      for (int kb = 0; kb < nkb_run; ++kb) {
+      int pre = 0;
+      if (it == 0) {
+        pre = nkb_run < STAGES ? nkb_run : STAGES;
+        for (int kb = 0; kb < pre; ++kb) {
+          const uint32_t fb = ptx::smem_u32(&full_bar[kb]);
+          ptx::mbar_expect_tx(fb, Sh::STAGE);
+          const int32_t xb = (int32_t)((int64_t)tile * a.nkbt + kbeg / KB + kb);
+          ptx::tma_load_3d(x_addr(kb, 0), &tx_hi, 0, 0, xb, fb);
+          if (X3) ptx::tma_load_3d(x_addr(kb, 1), &tx_lo, 0, 0, xb, fb);
+        }
+        ptx::pdl_wait();
+        // Our own predecessor is complete: the next half step may now be
+        // scheduled (its blocks take SMs as ours leave and prefetch V, which
+        // no tensor-core launch writes, before they wait for us).
+        ptx::pdl_launch_dependents();
+        for (int kb = 0; kb < pre; ++kb) {
+          const uint32_t fb = ptx::smem_u32(&full_bar[kb]);
+          const int32_t kc = (int32_t)(kbeg + (int64_t)kb * KB);
+          ptx::tma_load_2d(y_addr(kb, 0), &ty_hi, kc, 0, fb);
+          if (X3) ptx::tma_load_2d(y_addr(kb, 1), &ty_lo, kc, 0, fb);
+        }
+        issued = pre;
+      }
+      for (int kb = pre; kb < nkb_run; ++kb) {
         const int g = kb_base + kb;
         const int s = g % STAGES;
         const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
@@ -266,22 +312,26 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
       }
       // Always signal: also covers MMAs still in flight on the abort path.
       ptx::mma_commit(ptx::smem_u32(&acc_bar));
+    } else if (helper && !*(volatile int*)&s_abort) {
+      // ---------------- helpers: old rows and denominators of this slice ----
+      if (it > 0) {
+        tcepi::load_old<RPAD>(Os, a.ep, R, row0, rows, h);   // first tile: in the prologue
+      }
+      tcepi::compute_den<RPAD>(Qs, Os, den, a.Gpad, a.r, R, h);
     }
     __syncwarp();
     kb_base += nkb_run;
 
     // ---------------- accumulator -> shared memory ----------------
+    if (it == 0) ptx::pdl_wait();   // results of the previous launch are final
     const bool acc_ok = ptx::mbar_wait(ptx::smem_u32(&acc_bar), (uint32_t)it & 1u, kWaitLimitCycles);
     ptx::tc_fence_after();
     if (!acc_ok) atomicExch(&s_abort, 1);
     __syncthreads();
     const bool abort = *(volatile int*)&s_abort != 0;
 
-    float* Acc = reinterpret_cast<float*>(smem);                       // [128][LDA]  (S > 1)
-    float* Ns = S > 1 ? reinterpret_cast<float*>(smem + Sh::ACC) : Acc; // [R][LDN]
-    const int R = kBM / S;
-    float* Os = Ns + R * LDN;
-    float* Gs = Os + R * LDO;
+    float* Acc = reinterpret_cast<float*>(smem);                  // [128][LDA] (ring region)
+    float* Ns = reinterpret_cast<float*>(smem + Sh::ACC);         // [R][LDN]
     const int row = warp * 32 + lane;  // TMEM lane == tile row
     if (!abort && warp < 4) {
 #pragma unroll
@@ -293,60 +343,34 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
 #pragma unroll
           for (int j = 0; j < 16; ++j) v[j] = 0.f;
         }
-        if (S == 1) {
 #pragma unroll
-          for (int j = 0; j < 16; j += 4)
-            *reinterpret_cast<float4*>(&Ns[row * LDN + c * 16 + j]) =
-                make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; j += 4)
-            *reinterpret_cast<float4*>(&Acc[row * LDA + c * 16 + j]) =
-                make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-        }
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4*>(&Acc[row * LDA + c * 16 + j]) =
+              make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
       }
     }
     ptx::tc_fence_before();
     // Cluster barriers are executed the same number of times by every block
     // of a cluster, aborted or not, so no block can wait on a peer forever.
-    if (S > 1) {
-      cluster.sync();   // every block's partial tile is in its shared memory
-      if (!abort) {
-        // rows [q R, (q+1) R) of the tile: sum the S partial tiles in rank order
-        for (int i = threadIdx.x; i < R * (RPAD / 4); i += kThreads) {
-          const int m = i / (RPAD / 4), k4 = (i % (RPAD / 4)) * 4;
-          const float4* mine = reinterpret_cast<const float4*>(&Acc[(q * R + m) * LDA + k4]);
-          float4 v[8];
+    cluster.sync();   // every block's partial tile is in its shared memory
+    if (!abort) {
+      // rows [q R, (q+1) R) of the tile: sum the S partial tiles in rank order
+      for (int i = threadIdx.x; i < R * (RPAD / 4); i += kThreads) {
+        const int m = i / (RPAD / 4), k4 = (i % (RPAD / 4)) * 4;
+        const float4* mine = reinterpret_cast<const float4*>(&Acc[(q * R + m) * LDA + k4]);
+        float4 v[8];
 #pragma unroll
-          for (int s = 0; s < 8; ++s)
-            if (s < S) v[s] = *cluster.map_shared_rank(mine, s);   // all loads first
-          float4 sum = v[0];
+        for (int s = 0; s < 8; ++s)
+          if (s < S) v[s] = *cluster.map_shared_rank(mine, s);   // all loads first
+        float4 sum = v[0];
 #pragma unroll
-          for (int s = 1; s < 8; ++s)
-            if (s < S) { sum.x += v[s].x; sum.y += v[s].y; sum.z += v[s].z; sum.w += v[s].w; }
-          *reinterpret_cast<float4*>(&Ns[m * LDN + k4]) = sum;
-        }
+        for (int s = 1; s < 8; ++s)
+          if (s < S) { sum.x += v[s].x; sum.y += v[s].y; sum.z += v[s].z; sum.w += v[s].w; }
+        *reinterpret_cast<float4*>(&Ns[m * LDN + k4]) = sum;
       }
-      cluster.sync();   // peers are done reading this block's tile
-    } else {
-      __syncthreads();
     }
-
-    if (!abort && !gram_ready) {
-      // wait until every block has published its share of the Gram
-      if (threadIdx.x == 0) {
-        const uint64_t t0 = ptx::globaltimer();
-        while (ld_acquire(a.gctr) < a.gtarget) {
-          if (ptx::globaltimer() - t0 > kWaitLimitNs) { atomicExch(&s_abort, 1); break; }
-        }
-      }
-      __syncthreads();
-      gram_ready = true;
-    }
-    if (!*(volatile int*)&s_abort) {
-      float* P = a.ep.gram_part + ((int64_t)tile * S + q) * a.r * a.r;
-      mu_epilogue<RPAD, kThreads>(Ns, Os, Gs, R, m0 + (int64_t)q * R, P, a.ep);
-    }
+    cluster.sync();   // peers are done reading this block's tile
+    if (!*(volatile int*)&s_abort) tcepi::finish<RPAD, kThreads>(Ns, Os, den, a.ep, R, row0, rows);
     // The next tile's copies overwrite this shared memory through the async proxy.
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -515,11 +539,12 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
       if (err) *err = "split_k must be 1, 2, 4 or 8 for tensor-core precisions";
       return NMF_EINVAL;
     }
-    while (want > 1 && nkb < (int64_t)want) want /= 2;   // at most one split per k-block
+    while (want > 2 && nkb < (int64_t)want) want /= 2;   // at most one split per k-block
   }
-  for (int S = 1; S <= 8; S *= 2) {
+  if (want == 1) want = 2;   // a slice of at most 64 rows per block: clusters of >= 2
+  for (int S = 2; S <= 8; S *= 2) {
     if (want > 0 && S != want) continue;
-    if (S > 1 && nkb < (int64_t)S) continue;
+    if (S > 2 && nkb < (int64_t)S) continue;
     const int maxc = max_clusters(fn, smem, S, sms);
     if (maxc < 1) continue;
     const int G = maxc < pl.tiles ? maxc : pl.tiles;
@@ -566,24 +591,29 @@ cudaError_t tc_launch(const TcPlan& pl, const EpiArgs& ep, const TcGram& gr, int
   prm.S = pl.S; prm.tiles = pl.tiles; prm.nclusters = pl.nclusters; prm.kper = pl.kchunk;
   prm.nkbt = pl.nkbt;
   prm.ep = ep;
-  prm.gin = gr.gin; prm.gin_count = gr.gin_count;
-  prm.G32 = gr.G32; prm.G64 = gr.G64;
-  prm.gctr = gr.ctr; prm.gtarget = gr.target;
+  prm.Q = gr.Q; prm.q_layout = gr.q_layout; prm.ldq = gr.ldq; prm.QM = gr.QM;
+  prm.gpart = gr.gpart;
+  prm.Gpad = gr.Gpad; prm.G64 = gr.G64;
+  prm.ctr = gr.ctr; prm.base = gr.base;
   prm.err = err;
-  prm.ep.G = gr.G32;
 
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)pl.grid, 1, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
   cfg.dynamicSmemBytes = (size_t)pl.smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr;
-  attr.id = cudaLaunchAttributeClusterDimension;
-  attr.val.clusterDim.x = (unsigned)pl.S;
-  attr.val.clusterDim.y = 1;
-  attr.val.clusterDim.z = 1;
-  cfg.attrs = &attr;
-  cfg.numAttrs = 1;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)pl.S;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  // Programmatic dependent launch: this grid may start while the previous
+  // kernel in the stream drains; it waits (griddepcontrol.wait) before using
+  // that kernel's results.
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
   void* args[] = {(void*)&pl.x_hi, (void*)&pl.x_lo, (void*)&pl.y_hi, (void*)&pl.y_lo,
                   (void*)&prm};
   cudaError_t e = cudaLaunchKernelExC(&cfg, pl.fn, args);

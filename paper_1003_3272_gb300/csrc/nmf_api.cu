@@ -91,6 +91,8 @@ struct nmf_ctx {
   int gcount[2] = {0, 0};
   unsigned long long* gctr = nullptr;     // grid-wide counter of the tensor-core kernel
   unsigned long long gctr_host = 0;       // its value after every launch so far
+  float* GWpad = nullptr; float* GHpad = nullptr;   // rpad x rpad Grams (tensor-core form)
+  double* tc_gpart = nullptr;             // tensor-core prologue partials (one per block)
   // split-K
   float* part = nullptr;
   unsigned* counters = nullptr;
@@ -104,8 +106,10 @@ struct nmf_ctx {
   HalfPlan half[2];           // [0] right update (H), [1] left update (W)
   // CUDA-event timing by kind (nmf_profile_*)
   bool prof = false;
+  bool in_step = false;       // inside nmf_step (tensor-core launches timed as a group)
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_open;
+  struct Open { int kind; int launches; cudaEvent_t a, b; };
+  std::vector<Open> ev_open;
   double prof_ms[4] = {0, 0, 0, 0};
   int64_t prof_n[4] = {0, 0, 0, 0};
 };
@@ -151,12 +155,15 @@ cudaEvent_t take_event(nmf_ctx* c) {
 }
 
 // Brackets one region of work of `kind` with events when profiling is on.
+// `launches` kernels of that kind run inside the bracket (their mean
+// duration is total time / launches).
 struct ProfScope {
   nmf_ctx* c;
   int kind;
+  int launches;
   cudaEvent_t a = nullptr, b = nullptr;
-  ProfScope(nmf_ctx* c_, int k) : c(c_), kind(k) {
-    if (!c->prof) return;
+  ProfScope(nmf_ctx* c_, int k, int n = 1) : c(c_), kind(k), launches(n) {
+    if (!c->prof || n <= 0) return;
     a = take_event(c);
     b = take_event(c);
     if (a && b) cudaEventRecord(a, c->st);
@@ -164,19 +171,19 @@ struct ProfScope {
   ~ProfScope() {
     if (!c->prof || !a || !b) return;
     cudaEventRecord(b, c->st);
-    c->ev_open.push_back({kind, {a, b}});
+    c->ev_open.push_back({kind, launches, a, b});
   }
 };
 
 void prof_collect(nmf_ctx* c) {
   for (auto& it : c->ev_open) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, it.second.first, it.second.second) == cudaSuccess) {
-      c->prof_ms[it.first] += ms;
-      c->prof_n[it.first] += 1;
+    if (cudaEventElapsedTime(&ms, it.a, it.b) == cudaSuccess) {
+      c->prof_ms[it.kind] += ms;
+      c->prof_n[it.kind] += it.launches;
     }
-    c->ev_pool.push_back(it.second.first);
-    c->ev_pool.push_back(it.second.second);
+    c->ev_pool.push_back(it.a);
+    c->ev_pool.push_back(it.b);
   }
   (void)cudaGetLastError();
   c->ev_open.clear();
@@ -404,6 +411,13 @@ nmf_status build_ctx(nmf_ctx* c) {
     if ((s = dalloc(c, (void**)&c->gpart[f], gtiles[f] * rr * 4)) != NMF_OK) return s;
   if ((s = dalloc(c, (void**)&c->gctr, sizeof(unsigned long long))) != NMF_OK) return s;
   c->gctr_host = 0;
+  if (tc) {
+    const size_t rp2 = (size_t)c->rpad * c->rpad;
+    if ((s = dalloc(c, (void**)&c->GWpad, rp2 * 4)) != NMF_OK) return s;
+    if ((s = dalloc(c, (void**)&c->GHpad, rp2 * 4)) != NMF_OK) return s;
+    const size_t grid = (size_t)(hh.tc.grid > hw.tc.grid ? hh.tc.grid : hw.tc.grid);
+    if ((s = dalloc(c, (void**)&c->tc_gpart, grid * rr * 8)) != NMF_OK) return s;
+  }
   for (HalfPlan* h : {&hh, &hw}) h->ep.gram_part = c->gpart[h->own];
   if ((s = dalloc(c, (void**)&c->obj_parts, objective_parts() * 8)) != NMF_OK) return s;
   if ((s = dalloc(c, (void**)&c->f_dev, 8)) != NMF_OK) return s;
@@ -420,7 +434,7 @@ void free_ctx(nmf_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
   if (c->f_host) cudaFreeHost(c->f_host);
   if (c->err_host) cudaFreeHost(c->err_host);
-  for (auto& it : c->ev_open) { cudaEventDestroy(it.second.first); cudaEventDestroy(it.second.second); }
+  for (auto& it : c->ev_open) { cudaEventDestroy(it.a); cudaEventDestroy(it.b); }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   (void)cudaGetLastError();
   delete c;
@@ -459,29 +473,37 @@ nmf_status run_half(nmf_ctx* c, int which) {
        "gram reduce");
     launched(1);
   } else {
-    // The launch first reduces the other factor's partial Grams (left by the
-    // previous half step or by the start), then streams V and updates.
+    // The launch forms the other factor's Gram itself (prologue), then
+    // streams V and updates this factor.
     TcGram g;
-    g.gin = c->gpart[other];
-    g.gin_count = c->gcount[other];
-    g.G32 = other == 0 ? c->GW32 : c->GH32;
+    g.Q = other == 0 ? c->W : c->H;
+    g.q_layout = other == 0 ? 0 : 1;
+    g.ldq = other == 0 ? c->r : c->n;
+    g.QM = other == 0 ? c->p : c->n;
+    g.gpart = c->tc_gpart;
+    g.Gpad = other == 0 ? c->GWpad : c->GHpad;
     g.G64 = other == 0 ? c->GW64 : c->GH64;
     g.ctr = c->gctr;
-    c->gctr_host += (unsigned long long)h.tc.grid;
-    g.target = c->gctr_host;
-    ProfScope ps(c, 0);
+    g.base = c->gctr_host;
+    c->gctr_host += 2ull * (unsigned long long)h.tc.grid;
+    // timed per nmf_step (events between launches would break the
+    // programmatic dependent launch chain); a lone half step times itself
+    ProfScope ps(c, 0, c->in_step ? 0 : 1);
     CK(tc_launch(h.tc, h.ep, g, c->err_dev, c->st), "stream (tensor)");
     launched(1);
-    c->gcount[own] = h.tiles * h.tc.S;
   }
   return NMF_OK;
 }
 
-// Float64 Gram of factor f (0 = W, 1 = H) from its current partials.
+// Float64 Gram of factor f (0 = W, 1 = H), formed afresh from the factor.
 nmf_status reduce_gram(nmf_ctx* c, int f) {
+  const int64_t M = f == 0 ? c->p : c->n;
+  CK(launch_gram_tiles(f == 0 ? c->W : c->H, f == 0 ? kFactorRowMajor : kFactorColMajor, M,
+                       f == 0 ? c->r : c->n, c->r, c->gpart[f], 128, c->st), "gram tiles");
+  c->gcount[f] = (int)ceil_div(M, 128);
   CK(launch_gram_reduce(c->gpart[f], c->gcount[f], c->r, f == 0 ? c->GW32 : c->GH32,
                         f == 0 ? c->GW64 : c->GH64, c->st), "gram reduce");
-  launched(1);
+  launched(2);
   return NMF_OK;
 }
 
@@ -533,13 +555,17 @@ nmf_status nmf_step(nmf_ctx* c, int iters) {
   if (!c) { set_err(nullptr, "ctx is NULL"); return NMF_EINVAL; }
   if (iters < 0) { set_err(&c->err, "iters must be >= 0"); return NMF_EINVAL; }
   const int first = c->cfg.order == NMF_ORDER_H_FIRST ? 0 : 1;
-  for (int it = 0; it < iters; ++it) {
-    nmf_status s = run_half(c, first);
-    if (s != NMF_OK) return s;
-    s = run_half(c, 1 - first);
-    if (s != NMF_OK) return s;
+  const bool tc = c->cfg.prec != NMF_FP32;
+  // tensor-core launches chain by programmatic dependent launch: one bracket
+  ProfScope ps(c, 0, tc ? 2 * iters : 0);
+  c->in_step = tc;
+  nmf_status s = NMF_OK;
+  for (int it = 0; it < iters && s == NMF_OK; ++it) {
+    s = run_half(c, first);
+    if (s == NMF_OK) s = run_half(c, 1 - first);
   }
-  return NMF_OK;
+  c->in_step = false;
+  return s;
 }
 
 nmf_status nmf_objective(nmf_ctx* c, double* f_out) {

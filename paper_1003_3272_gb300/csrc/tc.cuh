@@ -28,19 +28,20 @@ struct TcPlan {
   CUtensorMap x_hi, x_lo, y_hi, y_lo;
 };
 
-// The other factor's Gram, reduced inside the launch from per-slice partials.
+// The other factor Q, whose Gram the launch forms itself (prologue), and
+// the grid-wide counter that orders the prologue's two phases.
 struct TcGram {
-  const float* gin;              // partials [gin_count][r][r]
-  int gin_count;
-  float* G32;                    // r x r, float32 (used by the epilogue)
-  double* G64;                   // r x r, float64
-  unsigned long long* ctr;       // grid-wide publication counter
-  unsigned long long target;     // counter value once every block published
+  const float* Q;                // W (p x r, layout 0) or H (r x n, layout 1)
+  int q_layout;
+  int64_t ldq;
+  int64_t QM;                    // rows of Q
+  double* gpart;                 // workspace, grid * r * r doubles
+  float* Gpad;                   // out: rpad x rpad float32 (zero padded)
+  double* G64;                   // out: r x r float64
+  unsigned long long* ctr;       // monotone counter
+  unsigned long long base;       // value before this launch (advances by 2 x grid)
 };
 
-// X_hi / X_lo: tile-blocked operand copies (blocks of 128 rows x 128 bytes,
-// block (tile, kb) at index tile * ceil(K / kblock) + kb); Y: K-major planes
-// with row pitch ldy.
 nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, const void* Y_hi,
                    const void* Y_lo, int64_t ldy, int64_t M, int64_t K, int r, int sms,
                    int user_split, TcPlan* plan, std::string* err);

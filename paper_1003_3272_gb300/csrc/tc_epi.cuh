@@ -1,0 +1,359 @@
+// Helper-warp work of the tensor-core half step (k_stream_tc.cu).
+//
+// While warps 0-1 stream V through the tensor cores, warps 2-7 (192 "helper"
+// threads, synchronised among themselves with named barrier 1) do all the
+// work of the multiply-divide update that does not depend on this launch's
+// product:
+//   * the r x r Gram matrix G of the *other* factor Q (W^T W for the H update,
+//     H H^T for the W update): each block sums an even share of Q's rows
+//     (float32 within 128-row windows, float64 across them), then each block
+//     adds up a share of the r^2 entries over all blocks' partials in float64
+//     in a fixed order (two grid-wide publication points);
+//   * for each output tile, the old rows of the factor being updated and the
+//     denominators  den[m,k] = sum_l old[m,l] G[l,k]  (the paper's V_n W_n
+//     W_n^t, resp. V^t V W_n, grouped through G; Section 3.1).
+// After the product lands, the whole block only forms
+//     new[m,k] = old[m,k] * num[m,k] / (den[m,k] + eps)
+// and writes the factor and its operand plane(s).
+#pragma once
+
+#include "epilogue.cuh"
+
+namespace nmf {
+namespace tcepi {
+
+constexpr int kHelpers = 192;     // warps 2-7
+constexpr int kHelperBase = 64;   // first helper thread
+constexpr int kRmax = 64;         // rows of a tile slice (cluster size >= 2)
+constexpr int kQsRows = 32;       // staging rows
+
+template <int RPAD> __host__ __device__ constexpr int ldq() { return RPAD + 4; }
+template <int RPAD> __host__ __device__ constexpr int ldo() { return RPAD + 1; }
+
+// Floats of the helpers' dedicated shared memory: staging Qs and old rows Os.
+// (The denominators stay in the helpers' registers.)
+template <int RPAD>
+__host__ __device__ constexpr int dedicated_floats() {
+  return kQsRows * ldq<RPAD>() + kRmax * ldo<RPAD>();
+}
+
+// Denominators of one helper thread: ranks kg*8 .. kg*8+7 of up to 8 rows
+// mg, mg + MG, ... of the slice (thread h: kg = h % KG, mg = h / KG).
+template <int RPAD>
+struct DenTile {
+  static constexpr int KG = RPAD / 8;
+  static constexpr int MG = kHelpers / KG;
+  float d[2][4][8];
+};
+
+__device__ __forceinline__ void helper_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kHelpers) : "memory");
+}
+
+// Values of rows [m0, m0 + nrows) (nrows <= kQsRows) of a factor, in the
+// order they land in Qs[row][k] (zero for k >= r and rows beyond nrows):
+// each thread owns up to SV values and issues all their loads at once.
+// layout 0: F[m * ldf + k];  layout 1: F[k * ldf + m].
+template <int RPAD>
+struct RowStage {
+  static constexpr int N = kQsRows * RPAD;
+  static constexpr int SV = (N + kHelpers - 1) / kHelpers;
+  float v[SV];
+  __device__ __forceinline__ void load(const float* F, int layout, int64_t ldf, int r,
+                                       int64_t m0, int nrows, int h) {
+#pragma unroll
+    for (int j = 0; j < SV; ++j) {
+      const int i = h + j * kHelpers;
+      int row, k;
+      if (layout == 0) { row = i / RPAD; k = i % RPAD; }
+      else             { k = i / kQsRows; row = i % kQsRows; }
+      v[j] = (i < N && row < nrows && k < r)
+                 ? (layout == 0 ? F[(m0 + row) * ldf + k] : F[(int64_t)k * ldf + m0 + row])
+                 : 0.f;
+    }
+  }
+  __device__ __forceinline__ void store(float* Qs, int layout, int h) const {
+    constexpr int LQ = ldq<RPAD>();
+#pragma unroll
+    for (int j = 0; j < SV; ++j) {
+      const int i = h + j * kHelpers;
+      if (i < N) {
+        int row, k;
+        if (layout == 0) { row = i / RPAD; k = i % RPAD; }
+        else             { k = i / kQsRows; row = i % kQsRows; }
+        Qs[row * LQ + k] = v[j];
+      }
+    }
+  }
+};
+
+// Partial Gram of rows [q0, q1) of Q, written to gpart (r x r doubles, both
+// triangles): float32 sums over windows of 128 rows, float64 across
+// windows.  Rows are staged 32 at a time; the next 32 are loaded into
+// registers while the current ones are multiplied.
+template <int RPAD>
+__device__ void gram_rows(float* Qs, const float* Q, int layout, int64_t ldq_g, int64_t q0,
+                          int64_t q1, int r, double* gpart, int h) {
+  constexpr int LQ = ldq<RPAD>();
+  constexpr int NBMAX = RPAD / 4;
+  constexpr int MAXB = (NBMAX * (NBMAX + 1) / 2 + kHelpers - 1) / kHelpers;
+  const int nbr = (r + 3) / 4;
+  const int npairs = nbr * (nbr + 1) / 2;
+  int kb[MAXB], lb[MAXB];
+#pragma unroll
+  for (int t = 0; t < MAXB; ++t) {
+    const int it = h + t * kHelpers;
+    int a = 0, rem = it < npairs ? it : 0;
+    while (rem >= nbr - a) { rem -= nbr - a; ++a; }
+    kb[t] = a;
+    lb[t] = a + rem;
+  }
+  float acc[MAXB][4][4];
+  double tot[MAXB][4][4];
+#pragma unroll
+  for (int t = 0; t < MAXB; ++t)
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) { acc[t][i][j] = 0.f; tot[t][i][j] = 0.0; }
+  RowStage<RPAD> st;
+  if (q0 < q1) st.load(Q, layout, ldq_g, r, q0, (int)min((int64_t)kQsRows, q1 - q0), h);
+  int in_window = 0;
+  for (int64_t s0 = q0; s0 < q1; s0 += kQsRows) {
+    helper_sync();              // previous rows consumed
+    st.store(Qs, layout, h);
+    helper_sync();
+    const int64_t s1 = s0 + kQsRows;
+    if (s1 < q1) st.load(Q, layout, ldq_g, r, s1, (int)min((int64_t)kQsRows, q1 - s1), h);
+#pragma unroll
+    for (int t = 0; t < MAXB; ++t) {
+      if (h + t * kHelpers >= npairs) continue;
+#pragma unroll 4
+      for (int m = 0; m < kQsRows; ++m) {
+        const float4 a = *reinterpret_cast<const float4*>(&Qs[m * LQ + kb[t] * 4]);
+        const float4 b = *reinterpret_cast<const float4*>(&Qs[m * LQ + lb[t] * 4]);
+        const float av[4] = {a.x, a.y, a.z, a.w};
+        const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[t][i][j] = fmaf(av[i], bv[j], acc[t][i][j]);
+      }
+    }
+    in_window += kQsRows;
+    if (in_window == 128 || s1 >= q1) {   // fold the window into float64
+#pragma unroll
+      for (int t = 0; t < MAXB; ++t)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) { tot[t][i][j] += (double)acc[t][i][j]; acc[t][i][j] = 0.f; }
+      in_window = 0;
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < MAXB; ++t) {
+    if (h + t * kHelpers >= npairs) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = kb[t] * 4 + i, l = lb[t] * 4 + j;
+        if (k < r && l < r) {
+          gpart[k * r + l] = tot[t][i][j];
+          gpart[l * r + k] = tot[t][i][j];
+        }
+      }
+  }
+}
+
+// Float64 sum, in a fixed order, of the `nparts` partials of entries
+// [e0, e1): thread h takes entry e0 + h % ne and partials g, g + ng, ...
+// (g = h / ne, ng = 192 / ne groups); the group sums are then added in
+// group order.  Writes G64 (r x r) and the zero-padded float32 copy Gpad.
+// `scratch` holds 192 doubles (shared).
+template <int RPAD>
+__device__ void gram_reduce_slice(const double* gpart, int nparts, int r, int e0, int e1,
+                                  double* G64, float* Gpad, double* scratch, int h) {
+  const int rr = r * r;
+  const int ne = e1 - e0;
+  if (ne <= 0) return;
+  for (int eb = e0; eb < e1; eb += kHelpers) {
+    const int nb = min(kHelpers, e1 - eb);
+    const int ng = kHelpers / nb;
+    const int g = h / nb, e = eb + h % nb;
+    double s = 0.0;
+    if (g < ng) {
+      for (int t0 = g; t0 < nparts; t0 += 16 * ng) {
+        double v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int t = t0 + j * ng;
+          v[j] = t < nparts ? __ldcg(gpart + (int64_t)t * rr + e) : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (t0 + j * ng < nparts) s += v[j];
+      }
+      scratch[g * nb + (h % nb)] = s;
+    }
+    helper_sync();
+    if (h < nb) {
+      double tot = 0.0;
+      for (int gg = 0; gg < ng; ++gg) tot += scratch[gg * nb + h];
+      G64[eb + h] = tot;
+      Gpad[((eb + h) / r) * RPAD + ((eb + h) % r)] = (float)tot;
+    }
+    helper_sync();
+  }
+}
+
+// Old rows of the slice into Os (issued early: they do not depend on G).
+template <int RPAD>
+__device__ void load_old(float* Os, const EpiArgs& e, int R, int64_t row0, int rows, int h) {
+  constexpr int LO = ldo<RPAD>();
+  constexpr int NV = (kRmax * RPAD + kHelpers - 1) / kHelpers;
+  const int r = e.r;
+  float v[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const int i = h + j * kHelpers;
+    int m, k;
+    if (e.layout == kFactorRowMajor) { m = i / RPAD; k = i % RPAD; }
+    else                             { k = i / R;    m = i % R; }
+    v[j] = (i < R * RPAD && m < rows && k < r)
+               ? (e.layout == kFactorRowMajor ? e.F[(row0 + m) * r + k]
+                                              : e.F[(int64_t)k * e.ldf + row0 + m])
+               : 0.f;
+  }
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const int i = h + j * kHelpers;
+    if (i < R * RPAD) {
+      int m, k;
+      if (e.layout == kFactorRowMajor) { m = i / RPAD; k = i % RPAD; }
+      else                             { k = i / R;    m = i % R; }
+      Os[m * LO + k] = v[j];
+    }
+  }
+}
+
+// den = old . G for the slice into the helper's registers (Os already
+// loaded; rows beyond the slice's valid rows and ranks beyond r are zero).  G rows are staged
+// 32 at a time through Qs from the padded float32 copy; the next 32 are in
+// flight while the current ones are used.
+template <int RPAD>
+__device__ void compute_den(float* Qs, const float* Os, DenTile<RPAD>& den, const float* Gpad,
+                            int r, int R, int h) {
+  constexpr int LQ = ldq<RPAD>();
+  constexpr int LO = ldo<RPAD>();
+  constexpr int NG = kQsRows * RPAD;
+  constexpr int GV = (NG + kHelpers - 1) / kHelpers;
+  constexpr int KG = RPAD / 8;
+  constexpr int MG = kHelpers / KG;
+  const int kg = h % KG, mg = h / KG;
+  const bool active = h < KG * MG;
+  auto& acc = den.d;    // up to 8 rows per thread (R <= 64, MG >= 12 for RPAD <= 128)
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[a][i][j] = 0.f;
+  float gv[GV];
+  auto gload = [&](int l0) {
+#pragma unroll
+    for (int j = 0; j < GV; ++j) {
+      const int i = h + j * kHelpers;
+      gv[j] = (i < NG && l0 + i / RPAD < r) ? __ldcg(Gpad + l0 * RPAD + i) : 0.f;
+    }
+  };
+  gload(0);
+  for (int l0 = 0; l0 < r; l0 += kQsRows) {
+    helper_sync();   // previous G rows consumed (and Os complete on entry)
+#pragma unroll
+    for (int j = 0; j < GV; ++j) {
+      const int i = h + j * kHelpers;
+      if (i < NG) Qs[(i / RPAD) * LQ + (i % RPAD)] = gv[j];
+    }
+    helper_sync();
+    if (l0 + kQsRows < r) gload(l0 + kQsRows);
+    const int nl = min(kQsRows, r - l0);
+    if (active) {
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        if (mg + 4 * a * MG >= R) break;
+        int mrow[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) mrow[i] = min(mg + (4 * a + i) * MG, R - 1);
+#pragma unroll 2
+        for (int l = 0; l < nl; ++l) {
+          const float4 g0 = *reinterpret_cast<const float4*>(&Qs[l * LQ + kg * 8]);
+          const float4 g1 = *reinterpret_cast<const float4*>(&Qs[l * LQ + kg * 8 + 4]);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float o = Os[mrow[i] * LO + l0 + l];
+            acc[a][i][0] = fmaf(o, g0.x, acc[a][i][0]); acc[a][i][1] = fmaf(o, g0.y, acc[a][i][1]);
+            acc[a][i][2] = fmaf(o, g0.z, acc[a][i][2]); acc[a][i][3] = fmaf(o, g0.w, acc[a][i][3]);
+            acc[a][i][4] = fmaf(o, g1.x, acc[a][i][4]); acc[a][i][5] = fmaf(o, g1.y, acc[a][i][5]);
+            acc[a][i][6] = fmaf(o, g1.z, acc[a][i][6]); acc[a][i][7] = fmaf(o, g1.w, acc[a][i][7]);
+          }
+        }
+      }
+    }
+  }
+}
+
+// new = old * num / (den + eps) for the slice (num in Ns[m][k], stride LN),
+// then the factor and its operand plane(s).  Pass 1 (helpers, their own
+// denominators): new values into Ns, and the row-major factor (W) directly.
+// Pass 2 (every thread of the block, rows fastest): the [k][m]-ordered
+// arrays -- the plane(s) and, for H, the factor.
+template <int RPAD, int NT>
+__device__ void finish(float* Ns, const float* Os, const DenTile<RPAD>& den, const EpiArgs& e,
+                       int R, int64_t row0, int rows) {
+  constexpr int LN = epi_ldn<RPAD>();
+  constexpr int LO = ldo<RPAD>();
+  constexpr int KG = DenTile<RPAD>::KG;
+  constexpr int MG = DenTile<RPAD>::MG;
+  const int r = e.r;
+  const int tid = threadIdx.x;
+  const int h = tid - kHelperBase;
+  if (h >= 0 && h < KG * MG) {
+    const int kg = h % KG, mg = h / KG;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int m = mg + (4 * a + i) * MG;
+        if (m >= rows) continue;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int k = kg * 8 + j;
+          const float d = __fadd_rn(den.d[a][i][j], e.eps);
+          v[j] = k < r ? __fdiv_rn(__fmul_rn(Os[m * LO + k], Ns[m * LN + k]), d) : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j += 4)
+          *reinterpret_cast<float4*>(&Ns[m * LN + kg * 8 + j]) =
+              make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        if (e.layout == kFactorRowMajor) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (kg * 8 + j < r) e.F[(row0 + m) * r + kg * 8 + j] = v[j];
+        }
+      }
+  }
+  __syncthreads();
+  for (int i = tid; i < rows * r; i += NT) {
+    const int k = i / rows, m = i % rows;
+    const float v = Ns[m * LN + k];
+    if (e.layout != kFactorRowMajor) e.F[(int64_t)k * e.ldf + row0 + m] = v;
+    store_plane(e, k, row0 + m, v);
+  }
+  (void)R;
+}
+
+}  // namespace tcepi
+}  // namespace nmf
