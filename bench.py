@@ -142,16 +142,34 @@ def algorithmic(prec, p, n, r):
     return bytes_, flops
 
 
+TC_SOURCES = ["k_stream_tc.cu", "tc_epi.cuh", "tc_ptx.cuh", "epilogue.cuh", "tc.cuh"]
+
+
+def kernel_source_digest():
+    """sha256 over the tensor-core kernel's sources: a recorded ncu traffic
+    figure is used only while the kernel is unchanged since its capture."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in TC_SOURCES:
+        with open(os.path.join(ROOT, "paper_1003_3272_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def read_traffic(kernel_key):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    from the committed ncu summary, or None when absent or stale."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     try:
         with open(path) as fh:
-            d = json.load(fh)
-        return d.get(kernel_key)
+            d = json.load(fh).get(kernel_key)
     except (OSError, ValueError):
         return None
+    if not d or d.get("kernel_digest") != kernel_source_digest():
+        return None
+    return d.get("traffic_bytes_per_launch")
 
 
 def run_gpu(args, ws, rank, local):
