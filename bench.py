@@ -9,6 +9,12 @@ and applies the relative-change stopping test.  Metric: MM updates (full
 iterations) per second, aggregated over all GPUs; each GPU solves its own
 replica (weak scaling, no collective in the data path).
 
+The headline line is the split-BF16x3 tensor-core form (the form that meets
+the 1e-5 relative objective bar); `by_precision` reports the plain FP32 form
+and TF32 / BF16 on the same workload, `batched` the 512-instance batched
+workload (grouped persistent launches), `accuracy` each form's objective
+error against the FP64 oracle.
+
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU
 oracle instead (the reference arm), on a bounded sample of the same workload.
 """
@@ -172,20 +178,18 @@ def read_traffic(kernel_key):
     return d.get("traffic_bytes_per_launch")
 
 
-def run_gpu(args, ws, rank, local):
-    import numpy as np
+def time_planted(pr, prec, steps, warmup, ws, local, sample_clocks=False, profile=True):
+    """Time `steps` benchmark steps of one precision on the planted problem.
+    Returns the measurement dict (updates/s, per-launch stream time, ...)."""
     import torch
     from paper_1003_3272_gb300 import nmf, synth
-
-    torch.cuda.set_device(local)
-    pr = synth.planted(iters=args.iters)
     p, n, r, iters = pr.p, pr.n, pr.r, pr.iters
     seed = synth.BASE_SEED + 1
     V = torch.from_numpy(pr.V).cuda()
     W = torch.empty(p, r, device="cuda")
     H = torch.empty(r, n, device="cuda")
     stream = torch.cuda.current_stream()
-    ctx = nmf.NMF(V, W, H, eps=pr.eps, prec=args.prec, seed=seed, init_from_seed=True,
+    ctx = nmf.NMF(V, W, H, eps=pr.eps, prec=prec, seed=seed, init_from_seed=True,
                   stream=stream)
     f_prev = [None]
 
@@ -195,64 +199,156 @@ def run_gpu(args, ws, rank, local):
         f = ctx.objective()
         # Section 3's stopping statistic on successive objective evaluations
         if f_prev[0] is not None:
-            _ = abs(f - f_prev[0]) / (abs(f_prev[0]) + 1.0)
+            _ = abs(f - f_prev[0]) / (abs(f_prev[0]) + 1.0) < 1e-9
         f_prev[0] = f
         return f
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-    ctx.profile(True)
-    sampler = ClockSampler(local)
+    if profile:
+        ctx.profile(True)
+    sampler = ClockSampler(local) if sample_clocks else None
     barrier(ws)
     torch.cuda.synchronize()
-    sampler.start()
+    if sampler:
+        sampler.start()
     l0 = nmf.kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    fs = []
-    for _ in range(args.steps):
-        fs.append(step())
+    fs = [step() for _ in range(steps)]
     e1.record(stream)
     torch.cuda.synchronize()
     launches = nmf.kernel_launches() - l0
     barrier(ws)
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    ms = max_over_ranks(ms, ws)
-    stream_ms, stream_n = ctx.profile_read(0)
-    gram_ms, gram_n = ctx.profile_read(1)
-    obj_ms, obj_n = ctx.profile_read(2)
-    prep_ms, prep_n = ctx.profile_read(3)
-    ctx.profile(False)
+    clocks = sampler.stop() if sampler else None
+    ms = max_over_ranks(e0.elapsed_time(e1), ws)
+    res = {"prec": prec, "ms": ms, "steps": steps, "launches": int(launches),
+           "clocks": clocks, "objective": fs[-1],
+           "value": iters * steps * ws / (ms / 1e3)}
+    if profile:
+        res["kinds"] = {k: ctx.profile_read(i) for i, k in
+                        enumerate(["stream_products", "gram_reductions", "objective", "restart"])}
+        ctx.profile(False)
+    ctx.close()
+    del V, W, H
+    torch.cuda.empty_cache()
+    return res
 
-    total_updates = iters * args.steps * ws
-    value = total_updates / (ms / 1e3)
+
+def roofline(prec, p, n, r, res, clocks):
     pk = peaks()
-    bytes_l, flops_l = algorithmic(args.prec, p, n, r)
-    avg_s = (stream_ms / max(stream_n, 1)) / 1e3
-    if args.prec == "fp32":
-        mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    bytes_l, flops_l = algorithmic(prec, p, n, r)
+    st_ms, st_n = res["kinds"]["stream_products"]
+    avg_s = (st_ms / max(st_n, 1)) / 1e3
+    if prec == "fp32":
+        mhz = (clocks or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
         peak = SMS * FFMA_PER_SM_PER_CLK * 2 * mhz * 1e6 / 1e12
         achieved = flops_l / avg_s / 1e12
         roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "peak_source": f"152 SMs x 128 FP32 FMA/clk x 2 x {mhz:.0f} MHz (median sampled SM clock)",
+                "peak_source": f"152 SMs x 128 FP32 FMA/clk x 2 x {mhz:.0f} MHz "
+                               "(median sampled SM clock)",
                 "kernel": "k_stream_simt"}
     else:
         peak = pk["hbm_gbs"]
         achieved = bytes_l / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": f"{pk['_source']} hbm_gbs",
+                "frac": round(achieved / peak, 4),
+                "peak_source": f"{pk['_source']} hbm_gbs (copy bandwidth, MEASURED_PEAKS.json)",
                 "kernel": "k_stream_tc"}
-    roof["traffic"] = read_traffic(f"{roof['kernel']}/{args.prec}/planted_8192x8192_r50")
+    roof["traffic"] = read_traffic(f"{roof['kernel']}/{prec}/planted_8192x8192_r50")
     roof["algorithmic_bytes_per_launch"] = int(bytes_l)
     roof["algorithmic_flops_per_launch"] = float(flops_l)
     roof["avg_launch_us"] = round(avg_s * 1e6, 2)
+    roof["launches_timed"] = int(st_n)
+    return roof
+
+
+def time_batched(prec, steps, warmup, iters, ws):
+    """The batched workload: 512 independent problems (p, n in 64..2048, r in
+    4..32), `iters` MM iterations per step through nmf_batched_step (one
+    grouped persistent launch per half step, CUDA graph)."""
+    import numpy as np
+    import torch
+    from paper_1003_3272_gb300 import nmf, synth
+    probs = synth.batch(iters=iters)
+    Vs = [torch.from_numpy(pr.V).cuda() for pr in probs]
+    Ws = [torch.from_numpy(pr.W0).cuda() for pr in probs]
+    Hs = [torch.from_numpy(pr.H0).cuda() for pr in probs]
+    b = nmf.Batch(Vs, Ws, Hs, prec=prec)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        b.step(iters)
+    torch.cuda.synchronize()
+    barrier(ws)
+    l0 = nmf.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        b.step(iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = nmf.kernel_launches() - l0
+    ms = max_over_ranks(e0.elapsed_time(e1), ws)
+    f = b.objective()
+    vb = {"fp32": 4, "tf32": 4, "bf16x3": 4, "bf16": 2}[prec]
+    bytes_it = sum(2 * pr.p * pr.n * vb for pr in probs)
+    per_it_s = ms / 1e3 / (steps * iters)
+    out = {"metric": "instance MM iterations/s", "precision": prec, "instances": len(probs),
+           "iters_per_step": iters, "steps": steps, "ms_per_step": round(ms / steps, 3),
+           "value": round(len(probs) * iters * steps * ws / (ms / 1e3), 1),
+           "unit": "instance-iterations/s",
+           "aggregate_gbs": round(bytes_it / per_it_s / 1e9, 1),
+           "hbm_frac": round(bytes_it / per_it_s / 1e9 / peaks()["hbm_gbs"], 4),
+           "V_bytes_per_iteration": int(bytes_it), "gpu_launches": int(launches),
+           "mean_objective": float(np.mean(f)),
+           "config": "synth.batch(): 512 instances, p,n ~ U{64..2048}, r ~ U{4..32}, "
+                     "V ~ U[0,1), seeded"}
+    b.close()
+    del Vs, Ws, Hs
+    torch.cuda.empty_cache()
+    return out
+
+
+def accuracy_check(precs):
+    """Relative objective error after 10 iterations against the float64
+    oracle on the planted problem at 1024 x 1024, r = 50 (same seeds)."""
+    import torch
+    from oracle import nmf_oracle as orc
+    from paper_1003_3272_gb300 import nmf, synth
+    pr = synth.planted(p=1024, n=1024, r=50, iters=10)
+    Wo, Ho, _, _ = orc.run(pr.V, pr.W0, pr.H0, 10, eps=pr.eps)
+    fo = orc.objective(pr.V, Wo, Ho)
+    out = {}
+    for prec in precs:
+        V = torch.from_numpy(pr.V).cuda()
+        W = torch.from_numpy(pr.W0).cuda()
+        H = torch.from_numpy(pr.H0).cuda()
+        with nmf.NMF(V, W, H, eps=pr.eps, prec=prec) as m:
+            m.step(10)
+            f = m.objective()
+        out[prec] = float(f"{abs(f - fo) / fo:.3e}")
+    return {"rel_objective_error_vs_fp64_oracle": out,
+            "case": "planted 1024x1024 r=50, 10 iterations from the seeded start"}
+
+
+def run_gpu(args, ws, rank, local):
+    import torch
+    from paper_1003_3272_gb300 import synth
+
+    torch.cuda.set_device(local)
+    pr = synth.planted(iters=args.iters)
+    p, n, r, iters = pr.p, pr.n, pr.r, pr.iters
+    stream = torch.cuda.current_stream()
+    main = time_planted(pr, args.prec, args.steps, args.warmup, ws, local, sample_clocks=True)
+    clocks = main["clocks"]
+    roof = roofline(args.prec, p, n, r, main, clocks)
 
     # End to end through the public one-call API with host buffers.
     e2e = None
     if not args.no_e2e:
+        from paper_1003_3272_gb300 import nmf
         Vh = torch.from_numpy(pr.V).pin_memory().numpy()
         Wh0 = torch.from_numpy(pr.W0).pin_memory().numpy()
         Hh0 = torch.from_numpy(pr.H0).pin_memory().numpy()
@@ -271,11 +367,14 @@ def run_gpu(args, ws, rank, local):
         e2e = {"value": round(iters * ne * ws / te, 2), "unit": "updates/s",
                "h2d_bytes_per_step": int(Vh.nbytes + Wh.nbytes + Hh.nbytes),
                "d2h_bytes_per_step": int(Wh.nbytes + Hh.nbytes + 8),
-               "steps": ne, "api": "nmf_solve (host V, W, H)"}
+               "steps": ne, "api": "nmf_solve (host V, W, H; allocation, operand copies, "
+                                   "200 iterations, objective, copies back)"}
 
+    kinds = main["kinds"]
     out = {
-        "metric": METRIC, "value": round(value, 2), "unit": "updates/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+        "metric": METRIC, "value": round(main["value"], 2), "unit": "updates/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(main["ms"] / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "tf32": "tf32", "bf16x3": "bf16x3", "bf16": "bf16"}[args.prec],
         "data": "synthetic (seeded planted low-rank matrix; no dataset)",
@@ -285,15 +384,30 @@ def run_gpu(args, ws, rank, local):
                    "l2": "inputs larger than L2 (V is 268 MB fp32; L2 129 MB)",
                    "step": "restart (operand copies + seeded W,H + Grams) + 200 MM "
                            "iterations + objective + stopping test"},
-        "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
-        "objective": fs[-1],
-        "breakdown_ms_per_step": {
-            "stream_products": round(stream_ms / args.steps, 3),
-            "gram_reductions": round(gram_ms / args.steps, 3),
-            "objective": round(obj_ms / args.steps, 3),
-            "restart": round(prep_ms / args.steps, 3)},
+        "roofline": roof, "e2e": e2e, "gpu_launches": main["launches"], "clocks": clocks,
+        "objective": main["objective"],
+        "breakdown_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in kinds.items()},
     }
-    ctx.close()
+    if not args.no_extras:
+        # the plain FP32 form and the other precisions on the same workload
+        by = {}
+        for prec in ["fp32", "tf32", "bf16x3", "bf16"]:
+            if prec == args.prec:
+                res, rf = main, roof
+            else:
+                res = time_planted(pr, prec, max(2, args.steps // 2), 2, ws, local)
+                rf = roofline(prec, p, n, r, res, clocks)
+            by[prec] = {"updates_per_s": round(res["value"], 1),
+                        "ms_per_step": round(res["ms"] / res["steps"], 3),
+                        "roofline_frac": rf["frac"], "roofline_bound": rf["bound"],
+                        "achieved": rf["achieved"], "unit": rf["unit"],
+                        "avg_launch_us": rf["avg_launch_us"]}
+        base = by["fp32"]["updates_per_s"]
+        for prec in by:
+            by[prec]["speedup_vs_fp32"] = round(by[prec]["updates_per_s"] / base, 2)
+        out["by_precision"] = by
+        out["batched"] = time_batched("bf16x3", max(2, args.steps // 2), 2, 20, ws)
+        out["accuracy"] = accuracy_check(["fp32", "tf32", "bf16x3", "bf16"])
     return out, pr
 
 
@@ -359,11 +473,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16x3", "bf16"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp32", "tf32", "bf16x3", "bf16"])
     ap.add_argument("--iters", type=int, default=200)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other precisions, the batched workload and the accuracy check")
     args = ap.parse_args()
 
     if args.impl == "reference":

@@ -1,0 +1,928 @@
+// Grouped persistent kernels of the batched form: many independent MM NMF
+// problems (Section 3.1, Eqs. (3.3)-(3.4)) updated together.
+//
+// Per half step of every instance b (H update, then W update):
+//   k_batched_gram : one block per instance forms the r_b x r_b Gram of the
+//                    factor that is *not* updated (float32 within 128-row
+//                    windows, float64 across them, fixed order).
+//   k_batched_tc   : a persistent grid walks a host-scheduled list of
+//                    (instance, 128-row tile) items; per item the whole K
+//                    range of the tile is streamed (TMA, tile-blocked V
+//                    copies) through tcgen05.mma into one of two tensor-
+//                    memory accumulators, so that the epilogue warps update
+//                    item i (num -> old * num / (old . G + eps)) while the
+//                    producer / MMA warps already stream item i + 1.
+// Tensor maps live in global memory (eight per instance).  Ranks up to 32.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <mutex>
+#include <numeric>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "nmf_internal.cuh"
+#include "tc_epi.cuh"
+#include "tc_ptx.cuh"
+
+namespace nmf {
+namespace {
+
+constexpr int kBR = 32;            // rank capacity (RPAD max)
+constexpr int kThreads = 192;      // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kBM = 128;
+constexpr uint64_t kWaitCycles = 3000ull * 1000 * 1000;
+constexpr int kSmemMax = 227 * 1024;
+
+struct BatchInst {
+  int64_t M[2], K[2];         // [half]: 0 = H update (M = n, K = p), 1 = W update (M = p, K = n)
+  int r, rpad;
+  float eps;
+  float* F[2];                // factor updated by each half: [0] H, [1] W
+  int64_t ldf[2];             // H: n; W: r
+  void* op_hi[2];             // its operand plane(s) [k][m]: [0] H plane, [1] W^T plane
+  void* op_lo[2];
+  int64_t ldop[2];
+  const float* Gpad[2];       // [half]: Gram of the other factor, kBR x kBR fp32 (padded)
+  int nkbt[2];                // k-blocks per tile row of X
+  int tmap;                   // first of eight maps: [half][x_hi, x_lo, y_hi, y_lo]
+  int plane;                  // PlaneKind
+};
+
+struct BatchParams {
+  const BatchInst* inst;
+  const CUtensorMap* maps;
+  const int2* items;          // (instance, tile)
+  const int* cta_off;         // items of block c: [cta_off[c], cta_off[c + 1])
+  int half;
+  int* err;
+};
+
+template <int PREC>
+struct BTraits;
+template <> struct BTraits<NMF_TF32>   { static constexpr int XPL = 1, KB = 32, FMT = 2; };
+template <> struct BTraits<NMF_BF16X3> { static constexpr int XPL = 2, KB = 64, FMT = 1; };
+template <> struct BTraits<NMF_BF16>   { static constexpr int XPL = 1, KB = 64, FMT = 1; };
+
+template <int PREC>
+struct BShape {
+  static constexpr int XPL = BTraits<PREC>::XPL;
+  static constexpr int X_BYTES = kBM * 128;
+  static constexpr int Y_BYTES = kBR * 128;
+  static constexpr int STAGE = XPL * (X_BYTES + Y_BYTES);
+  static constexpr int GS = kBR * kBR * 4;                 // the instance's Gram
+  static constexpr int STAGES_RAW = (kSmemMax - GS - 2048) / STAGE;
+  static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
+  static constexpr int SMEM = STAGES * STAGE + GS + 1024;
+};
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ __forceinline__ void plane_store(int plane, void* hi, void* lo, int64_t off, float v) {
+  if (plane == kPlaneTF32) {
+    static_cast<float*>(hi)[off] = round_tf32(v);
+  } else {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    static_cast<__nv_bfloat16*>(hi)[off] = h;
+    if (plane == kPlaneBF16x2)
+      static_cast<__nv_bfloat16*>(lo)[off] = __float2bfloat16_rn(__fsub_rn(v, __bfloat162float(h)));
+  }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1) k_batched_tc(const BatchParams a) {
+  using Sh = BShape<PREC>;
+  constexpr int STAGES = Sh::STAGES;
+  constexpr int KB = BTraits<PREC>::KB;
+  constexpr bool X3 = PREC == NMF_BF16X3;
+  constexpr uint32_t IDESC0 = ptx::idesc(BTraits<PREC>::FMT, kBM, 16) & ~(0x3Fu << 17);
+
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t accf[2];     // accumulator ready (MMA -> epilogue)
+  __shared__ __align__(8) uint64_t acce[2];     // accumulator drained (epilogue -> MMA)
+  __shared__ __align__(8) uint64_t done_bar;    // all MMAs of this block complete
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_abort;
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sbase = ptx::smem_u32(smem);
+  float* Gs = reinterpret_cast<float*>(smem + STAGES * Sh::STAGE);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int half = a.half;
+  const int i0 = a.cta_off[blockIdx.x], i1 = a.cta_off[blockIdx.x + 1];
+
+  auto x_addr = [&](int s, int plane) { return sbase + s * Sh::STAGE + plane * Sh::X_BYTES; };
+  auto y_addr = [&](int s, int plane) {
+    return sbase + s * Sh::STAGE + Sh::XPL * Sh::X_BYTES + plane * Sh::Y_BYTES;
+  };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      ptx::mbar_init(ptx::smem_u32(&full_bar[s]), 1);
+      ptx::mbar_init(ptx::smem_u32(&empty_bar[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(ptx::smem_u32(&accf[b]), 1);
+      ptx::mbar_init(ptx::smem_u32(&acce[b]), 128);
+    }
+    ptx::mbar_init(ptx::smem_u32(&done_bar), 1);
+    s_abort = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(ptx::smem_u32(&tmem_slot), 2 * kBR);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer: every k-block of every item ----------
+    ptx::pdl_wait();
+    ptx::pdl_launch_dependents();
+    int g = 0;
+    for (int i = i0; i < i1 && !*(volatile int*)&s_abort; ++i) {
+      const int2 it = a.items[i];
+      const BatchInst& B = a.inst[it.x];
+      const CUtensorMap* mp = a.maps + B.tmap + 4 * half;
+      const int nkb = B.nkbt[half];
+      const uint32_t bytes = Sh::XPL * (Sh::X_BYTES + B.rpad * 128);
+      for (int kb = 0; kb < nkb; ++kb, ++g) {
+        const int s = g % STAGES;
+        const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+        if (!ptx::mbar_wait(ptx::smem_u32(&empty_bar[s]), ph ^ 1u, kWaitCycles)) {
+          atomicExch(&s_abort, 1);
+          break;
+        }
+        const uint32_t fb = ptx::smem_u32(&full_bar[s]);
+        ptx::mbar_expect_tx(fb, bytes);
+        const int32_t xb = (int32_t)((int64_t)it.y * nkb + kb);
+        ptx::tma_load_3d(x_addr(s, 0), mp + 0, 0, 0, xb, fb);
+        if (X3) ptx::tma_load_3d(x_addr(s, 1), mp + 1, 0, 0, xb, fb);
+        ptx::tma_load_2d(y_addr(s, 0), mp + 2, kb * KB, 0, fb);
+        if (X3) ptx::tma_load_2d(y_addr(s, 1), mp + 3, kb * KB, 0, fb);
+      }
+    }
+    // drain: the last loads of each stage have landed
+    for (int gg = g - 1; gg >= 0 && gg >= g - STAGES; --gg)
+      if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[gg % STAGES]), (uint32_t)(gg / STAGES) & 1u,
+                          kWaitCycles))
+        atomicExch(&s_abort, 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    int g = 0;
+    for (int i = i0; i < i1; ++i) {
+      const int buf = (i - i0) & 1;
+      const uint32_t use = (uint32_t)((i - i0) >> 1);
+      if (*(volatile int*)&s_abort) break;
+      if (!ptx::mbar_wait(ptx::smem_u32(&acce[buf]), (use & 1u) ^ 1u, kWaitCycles)) {
+        atomicExch(&s_abort, 1);
+        break;
+      }
+      ptx::tc_fence_after();
+      const int2 it = a.items[i];
+      const BatchInst& B = a.inst[it.x];
+      const int nkb = B.nkbt[half];
+      const uint32_t idesc = IDESC0 | ((uint32_t)(B.rpad >> 3) << 17);
+      const uint32_t td = tmem + (uint32_t)(buf * kBR);
+      bool ok = true;
+      for (int kb = 0; kb < nkb; ++kb, ++g) {
+        const int s = g % STAGES;
+        const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+        if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[s]), ph, kWaitCycles)) {
+          atomicExch(&s_abort, 1);
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t ah = ptx::sdesc_sw128(x_addr(s, 0) + kk * 32);
+          const uint64_t bh = ptx::sdesc_sw128(y_addr(s, 0) + kk * 32);
+          const uint32_t acc = (kb | kk) != 0;
+          if (PREC == NMF_TF32) {
+            ptx::mma_tf32(td, ah, bh, idesc, acc);
+          } else {
+            ptx::mma_bf16(td, ah, bh, idesc, acc);
+            if (X3) {
+              ptx::mma_bf16(td, ah, ptx::sdesc_sw128(y_addr(s, 1) + kk * 32), idesc, 1);
+              ptx::mma_bf16(td, ptx::sdesc_sw128(x_addr(s, 1) + kk * 32), bh, idesc, 1);
+            }
+          }
+        }
+        ptx::mma_commit(ptx::smem_u32(&empty_bar[s]));
+      }
+      ptx::mma_commit(ptx::smem_u32(&accf[buf]));
+      if (!ok) break;
+    }
+    ptx::mma_commit(ptx::smem_u32(&done_bar));
+  } else if (warp >= 2) {
+    // ---------------- epilogue warps (128 threads) ----------------
+    const int et = threadIdx.x - 64;
+    const int quarter = warp & 3;                 // TMEM lanes 32 * (warp % 4)
+    const int row = quarter * 32 + lane;
+    ptx::pdl_wait();                              // the factors of the previous launch are final
+    for (int i = i0; i < i1; ++i) {
+      const int buf = (i - i0) & 1;
+      const uint32_t use = (uint32_t)((i - i0) >> 1);
+      const int2 it = a.items[i];
+      const BatchInst& B = a.inst[it.x];
+      const int r = B.r;
+      // the instance's Gram (kBR x kBR) into shared memory
+      epi_sync();
+      {
+        float gv[kBR * kBR / 128];
+#pragma unroll
+        for (int j = 0; j < kBR * kBR / 128; ++j) gv[j] = __ldcg(B.Gpad[half] + et + 128 * j);
+#pragma unroll
+        for (int j = 0; j < kBR * kBR / 128; ++j) Gs[et + 128 * j] = gv[j];
+      }
+      bool ok = ptx::mbar_wait(ptx::smem_u32(&accf[buf]), use & 1u, kWaitCycles);
+      ok = __all_sync(0xffffffffu, ok);   // tensor-memory loads are warp-collective
+      if (!ok) atomicExch(&s_abort, 1);
+      ptx::tc_fence_after();
+      float num[kBR];
+      if (ok) {
+        ptx::tmem_ld16(tmem + (uint32_t)(buf * kBR) + ((uint32_t)(quarter * 32) << 16), num);
+        if (B.rpad > 16)
+          ptx::tmem_ld16(tmem + (uint32_t)(buf * kBR + 16) + ((uint32_t)(quarter * 32) << 16),
+                         num + 16);
+      }
+      ptx::tc_fence_before();
+      ptx::mbar_arrive(ptx::smem_u32(&acce[buf]));
+      epi_sync();   // Gs complete; an expired wait is visible to all epilogue threads
+      if (*(volatile int*)&s_abort) break;
+      const int64_t M = B.M[half];
+      const int64_t m = (int64_t)it.y * kBM + row;
+      if (m < M) {
+        float old[kBR];
+        float* F = B.F[half];
+        const int64_t ldf = B.ldf[half];
+#pragma unroll
+        for (int k = 0; k < kBR; ++k)
+          old[k] = k < r ? (half == 0 ? F[(int64_t)k * ldf + m] : F[m * ldf + k]) : 0.f;
+#pragma unroll
+        for (int k = 0; k < kBR; ++k) {
+          if (k >= r) break;
+          float den = 0.f;
+#pragma unroll
+          for (int l = 0; l < kBR; ++l)
+            if (l < r) den = fmaf(old[l], Gs[l * kBR + k], den);
+          den = __fadd_rn(den, B.eps);
+          const float v = __fdiv_rn(__fmul_rn(old[k], num[k]), den);
+          if (half == 0) F[(int64_t)k * ldf + m] = v;
+          else           F[m * ldf + k] = v;
+          plane_store(B.plane, B.op_hi[half], B.op_lo[half], (int64_t)k * B.ldop[half] + m, v);
+        }
+      }
+    }
+  }
+  __syncwarp();
+  // every MMA of this block has completed before tensor memory is freed
+  if (threadIdx.x == 32 &&
+      !ptx::mbar_wait(ptx::smem_u32(&done_bar), 0, kWaitCycles))
+    atomicExch(&s_abort, 1);
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) ptx::tmem_dealloc(tmem, 2 * kBR);
+  if (*(volatile int*)&s_abort && threadIdx.x == 0) atomicExch(a.err, (int)NMF_ETIMEOUT);
+}
+
+// Gram of the factor that the half step does not update, one block per
+// instance: float32 within 128-row windows, float64 across (tcepi::gram_rows),
+// then the padded float32 copy used by the epilogue.
+struct GramInst {
+  const float* Q;            // W (layout 0, ldq = r) or H (layout 1, ldq = n)
+  int layout;
+  int64_t ldq, QM;
+  int r;
+  double* G64;               // r x r
+  float* Gpad;               // kBR x kBR
+};
+
+__global__ void __launch_bounds__(192) k_batched_gram(const GramInst* gi) {
+  __shared__ __align__(16) float Qs[tcepi::kQsRows * tcepi::ldq<kBR>()];
+  const GramInst g = gi[blockIdx.x];
+  tcepi::gram_rows<kBR>(Qs, g.Q, g.layout, g.ldq, 0, g.QM, g.r, g.G64, threadIdx.x);
+  __threadfence_block();
+  __syncthreads();
+  for (int q = threadIdx.x; q < kBR * kBR; q += blockDim.x) {
+    const int l = q / kBR, k = q % kBR;
+    g.Gpad[q] = (l < g.r && k < g.r) ? (float)g.G64[l * g.r + k] : 0.f;
+  }
+  // the next kernel may be scheduled; it waits for this grid before reading
+  ptx::pdl_launch_dependents();
+}
+
+// Objective of every instance: f_b = ||V_b - W_b H_b||_F^2, tiles of 64 x 128
+// of all instances in one grid; per-tile float64 partials summed per
+// instance in tile order.  Same per-entry arithmetic as k_objective.
+struct ObjInst {
+  const float* V;
+  const float* W;
+  const float* H;
+  int64_t p, n;
+  int r;
+  int tile0;                 // first global tile index of this instance
+  int tiles_n;               // tiles along n
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__global__ void __launch_bounds__(256) k_batched_objective(const ObjInst* oi, int count,
+                                                           const int* tile_inst, int ntiles,
+                                                           double* tile_part) {
+  __shared__ float Ws[64][kBR + 1];
+  __shared__ float Hs[kBR][128];
+  __shared__ double red[256];
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const ObjInst o = oi[tile_inst[t]];
+    const int lt = t - o.tile0;
+    const int64_t i0 = (int64_t)(lt / o.tiles_n) * 64, j0 = (int64_t)(lt % o.tiles_n) * 128;
+    __syncthreads();
+    for (int q = tid; q < 64 * kBR; q += 256) {
+      const int m = q / kBR, k = q % kBR;
+      Ws[m][k] = (i0 + m < o.p && k < o.r) ? o.W[(i0 + m) * o.r + k] : 0.f;
+    }
+    for (int q = tid; q < kBR * 128; q += 256) {
+      const int k = q / 128, c = q % 128;
+      Hs[k][c] = (j0 + c < o.n && k < o.r) ? o.H[(int64_t)k * o.n + j0 + c] : 0.f;
+    }
+    __syncthreads();
+    float sq[32];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int64_t i = i0 + ty + 8 * a, j = j0 + tx + 32 * b;
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int k = 0; k < kBR; k += 2) {
+          s0 = fmaf(Ws[ty + 8 * a][k], Hs[k][tx + 32 * b], s0);
+          s1 = fmaf(Ws[ty + 8 * a][k + 1], Hs[k + 1][tx + 32 * b], s1);
+        }
+        float hi, lo;
+        two_sum(s0, s1, hi, lo);
+        const float v = (i < o.p && j < o.n) ? o.V[i * o.n + j] : 0.f;
+        const float d = (i < o.p && j < o.n) ? __fsub_rn(__fsub_rn(v, hi), lo) : 0.f;
+        sq[a * 4 + b] = __fmul_rn(d, d);
+      }
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1)
+#pragma unroll
+      for (int q = 0; q < w; ++q) sq[q] = __fadd_rn(sq[q], sq[q + w]);
+    red[tid] = (double)sq[0];
+    __syncthreads();
+    for (int w = 128; w >= 1; w >>= 1) {
+      if (tid < w) red[tid] += red[tid + w];
+      __syncthreads();
+    }
+    if (tid == 0) tile_part[t] = red[0];
+  }
+  (void)count;
+}
+
+__global__ void k_batched_obj_sum(const ObjInst* oi, int count, const double* tile_part,
+                                  double* f) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  const ObjInst o = oi[b];
+  const int nt = (int)(ceil_div(o.p, 64) * o.tiles_n);
+  double s = 0.0;
+  for (int t = 0; t < nt; ++t) s += tile_part[o.tile0 + t];
+  f[b] = s;
+}
+
+}  // namespace
+}  // namespace nmf
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+using namespace nmf;
+
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+    (void)cudaGetLastError();
+  });
+  return fn;
+}
+
+bool map_blocked(CUtensorMap* m, const void* base, bool bf16, int64_t nblocks) {
+  EncodeTiled enc = encode_fn();
+  if (!enc) return false;
+  const int esz = bf16 ? 2 : 4;
+  cuuint64_t dims[3] = {(cuuint64_t)(128 / esz), 128, (cuuint64_t)nblocks};
+  cuuint64_t strides[2] = {128, 128 * 128};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / esz), 128, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+             const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool map_plane(CUtensorMap* m, const void* base, bool bf16, int64_t K, int rows, int64_t ld,
+               int box_rows) {
+  EncodeTiled enc = encode_fn();
+  if (!enc) return false;
+  const int esz = bf16 ? 2 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * esz)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+             const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+thread_local std::string g_batch_err;
+
+}  // namespace
+
+struct nmf_batch {
+  int count = 0;
+  nmf_precision prec = NMF_BF16X3;
+  cudaStream_t st = nullptr;
+  int sms = 0;
+  std::vector<nmf_config> cfg;
+  std::vector<const float*> V;
+  std::vector<float*> W, H;
+  std::vector<void*> allocs;
+  // device tables
+  BatchInst* d_inst = nullptr;
+  CUtensorMap* d_maps = nullptr;
+  int2* d_items[2] = {nullptr, nullptr};
+  int* d_off[2] = {nullptr, nullptr};
+  int grid[2] = {0, 0};
+  GramInst* d_gram[2] = {nullptr, nullptr};
+  ObjInst* d_obj = nullptr;
+  int* d_tile_inst = nullptr;
+  int obj_tiles = 0;
+  double* d_tile_part = nullptr;
+  double* d_f = nullptr;
+  double* h_f = nullptr;
+  int* d_err = nullptr;
+  int* h_err = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  std::string schedule = "lpt";
+  std::string err;
+};
+
+namespace {
+
+nmf_status bfail(nmf_batch* b, nmf_status s, const std::string& why) {
+  if (b) b->err = why;
+  g_batch_err = why;
+  record_error(why.c_str());
+  return s;
+}
+
+cudaError_t balloc(nmf_batch* b, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) return e;
+  b->allocs.push_back(*p);
+  return cudaMemsetAsync(*p, 0, bytes ? bytes : 16, b->st);
+}
+
+// Work schedule of one half step: items (instance, tile) distributed over
+// `grid` blocks.  "lpt": longest items first onto the least-loaded block;
+// "rr": items in instance order, round robin.  Cost of an item = k-blocks.
+void make_schedule(const std::vector<std::pair<int, int>>& items, const std::vector<int>& cost,
+                   int grid, const std::string& policy, std::vector<int2>& out,
+                   std::vector<int>& off) {
+  std::vector<std::vector<int>> per(grid);
+  if (policy == "rr") {
+    for (size_t i = 0; i < items.size(); ++i) per[i % grid].push_back((int)i);
+  } else {
+    std::vector<int> order(items.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<long long> load(grid, 0);
+    for (int i : order) {
+      int best = 0;
+      for (int c = 1; c < grid; ++c)
+        if (load[c] < load[best]) best = c;
+      per[best].push_back(i);
+      load[best] += cost[i] + 2;   // + per-item epilogue / pipeline overhead
+    }
+  }
+  out.clear();
+  off.assign(grid + 1, 0);
+  for (int c = 0; c < grid; ++c) {
+    off[c] = (int)out.size();
+    for (int i : per[c]) out.push_back(make_int2(items[i].first, items[i].second));
+  }
+  off[grid] = (int)out.size();
+}
+
+template <int PREC>
+cudaError_t launch_batched_tc(nmf_batch* b, int half) {
+  auto kern = k_batched_tc<PREC>;
+  static bool done = false;
+  if (!done) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         BShape<PREC>::SMEM);
+    if (e != cudaSuccess) return e;
+    done = true;
+  }
+  BatchParams prm{b->d_inst, b->d_maps, b->d_items[half], b->d_off[half], half, b->d_err};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)b->grid[half]);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = BShape<PREC>::SMEM;
+  cfg.stream = b->st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, prm);
+}
+
+cudaError_t launch_half(nmf_batch* b, int half) {
+  // Gram of the other factor: half 0 (H update) needs W^T W, half 1 needs H H^T
+  k_batched_gram<<<b->count, 192, 0, b->st>>>(b->d_gram[half]);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  count_launches(2);
+  switch (b->prec) {
+    case NMF_TF32: return launch_batched_tc<NMF_TF32>(b, half);
+    case NMF_BF16X3: return launch_batched_tc<NMF_BF16X3>(b, half);
+    case NMF_BF16: return launch_batched_tc<NMF_BF16>(b, half);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t run_iteration(nmf_batch* b) {
+  cudaError_t e = launch_half(b, 0);
+  if (e != cudaSuccess) return e;
+  return launch_half(b, 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+nmf_status nmf_batched_init(int count, const nmf_config* cfgs, const float* const* V,
+                            float* const* W, float* const* H, void* stream, nmf_batch** out) {
+  if (!out) return bfail(nullptr, NMF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !cfgs || !V || !W || !H) return bfail(nullptr, NMF_EINVAL, "bad arguments");
+  const nmf_precision prec = cfgs[0].prec;
+  if (prec != NMF_TF32 && prec != NMF_BF16X3 && prec != NMF_BF16)
+    return bfail(nullptr, NMF_EUNSUPPORTED,
+                 "the grouped kernel runs the tensor-core precisions (TF32, BF16X3, BF16)");
+  for (int i = 0; i < count; ++i) {
+    const nmf_config& c = cfgs[i];
+    if (c.prec != prec) return bfail(nullptr, NMF_EINVAL, "all instances need the same precision");
+    if (c.p < 1 || c.n < 1 || c.r < 1 || c.r > kBR || c.r > c.p || c.r > c.n)
+      return bfail(nullptr, NMF_EINVAL, "each instance needs 1 <= r <= min(p, n, 32)");
+    if (!(c.eps >= 0.f)) return bfail(nullptr, NMF_EINVAL, "eps must be >= 0");
+    if (c.order != NMF_ORDER_H_FIRST)
+      return bfail(nullptr, NMF_EINVAL, "the batched form updates H first");
+    if (!V[i] || !W[i] || !H[i]) return bfail(nullptr, NMF_EINVAL, "null V, W or H");
+    if (c.p > INT32_MAX / 2 || c.n > INT32_MAX / 2) return bfail(nullptr, NMF_EINVAL, "too large");
+  }
+  int dev = 0, major = 0, minor = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (major != 10 || minor != 3)
+    return bfail(nullptr, NMF_EUNSUPPORTED, "the grouped kernel needs an sm_103 GPU");
+
+  nmf_batch* b = new nmf_batch;
+  b->count = count;
+  b->prec = prec;
+  b->st = static_cast<cudaStream_t>(stream);
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  b->cfg.assign(cfgs, cfgs + count);
+  b->V.assign(V, V + count);
+  b->W.assign(W, W + count);
+  b->H.assign(H, H + count);
+  auto fail_cuda = [&](cudaError_t e, const char* what) {
+    std::string why = std::string(what) + ": " + cudaGetErrorString(e);
+    (void)cudaGetLastError();
+    nmf_batched_destroy(b);
+    return bfail(nullptr, e == cudaErrorMemoryAllocation ? NMF_ENOMEM : NMF_ECUDA, why);
+  };
+  const bool bf = prec != NMF_TF32;
+  const int elem = bf ? 2 : 4;
+  const int kbe = 128 / elem;
+  const int plane = prec == NMF_BF16X3 ? kPlaneBF16x2 : (prec == NMF_BF16 ? kPlaneBF16 : kPlaneTF32);
+  std::vector<BatchInst> inst(count);
+  std::vector<CUtensorMap> maps(8 * (size_t)count);
+  std::vector<GramInst> gram[2];
+  gram[0].resize(count);
+  gram[1].resize(count);
+  cudaError_t e;
+  for (int i = 0; i < count; ++i) {
+    const nmf_config& c = cfgs[i];
+    const int64_t p = c.p, n = c.n;
+    const int r = c.r, rpad = rank_pad16(r);
+    const int64_t ld_n = round_up(n, 16 / elem), ld_p = round_up(p, 16 / elem);
+    const int64_t nkb_n = ceil_div(n, kbe), nkb_p = ceil_div(p, kbe);
+    const size_t bw = (size_t)ceil_div(p, 128) * nkb_n * 128 * 128;   // V blocked (M = p)
+    const size_t bh = (size_t)ceil_div(n, 128) * nkb_p * 128 * 128;   // V^T blocked (M = n)
+    void *xw = nullptr, *xwl = nullptr, *xh = nullptr, *xhl = nullptr;
+    void *wop = nullptr, *wopl = nullptr, *hop = nullptr, *hopl = nullptr;
+    double *gw64 = nullptr, *gh64 = nullptr;
+    float *gwp = nullptr, *ghp = nullptr;
+    if ((e = balloc(b, &xw, bw)) != cudaSuccess) return fail_cuda(e, "cudaMalloc");
+    if ((e = balloc(b, &xh, bh)) != cudaSuccess) return fail_cuda(e, "cudaMalloc");
+    if (prec == NMF_BF16X3) {
+      if ((e = balloc(b, &xwl, bw)) != cudaSuccess) return fail_cuda(e, "cudaMalloc");
+      if ((e = balloc(b, &xhl, bh)) != cudaSuccess) return fail_cuda(e, "cudaMalloc");
+    }
+    if ((e = balloc(b, &wop, (size_t)rpad * ld_p * elem)) != cudaSuccess) return fail_cuda(e, "cudaMalloc");
+    if ((e = balloc(b, &hop, (size_t)rpad * ld_n * elem)) != cudaSuccess) return fail_cuda(e, "cudaMalloc");
+    if (prec == NMF_BF16X3) {
+      if ((e = balloc(b, &wopl, (size_t)rpad * ld_p * elem)) != cudaSuccess) return fail_cuda(e, "cudaMalloc");
+      if ((e = balloc(b, &hopl, (size_t)rpad * ld_n * elem)) != cudaSuccess) return fail_cuda(e, "cudaMalloc");
+    }
+    if ((e = balloc(b, (void**)&gw64, (size_t)r * r * 8)) != cudaSuccess) return fail_cuda(e, "cudaMalloc");
+    if ((e = balloc(b, (void**)&gh64, (size_t)r * r * 8)) != cudaSuccess) return fail_cuda(e, "cudaMalloc");
+    if ((e = balloc(b, (void**)&gwp, (size_t)kBR * kBR * 4)) != cudaSuccess) return fail_cuda(e, "cudaMalloc");
+    if ((e = balloc(b, (void**)&ghp, (size_t)kBR * kBR * 4)) != cudaSuccess) return fail_cuda(e, "cudaMalloc");
+    // operand copies of V and planes of the starting factors
+    if ((e = launch_operand_blocked(V[i], p, n, n, false, !bf, xw, xwl, nkb_n, kbe, b->st)) != cudaSuccess ||
+        (e = launch_operand_blocked(V[i], p, n, n, true, !bf, xh, xhl, nkb_p, kbe, b->st)) != cudaSuccess ||
+        (e = launch_factor_planes(W[i], kFactorRowMajor, p, r, r, wop, wopl, ld_p, plane, b->st)) != cudaSuccess ||
+        (e = launch_factor_planes(H[i], kFactorColMajor, n, n, r, hop, hopl, ld_n, plane, b->st)) != cudaSuccess)
+      return fail_cuda(e, "prepare");
+    count_launches(4);
+    BatchInst& B = inst[i];
+    B.M[0] = n; B.K[0] = p; B.M[1] = p; B.K[1] = n;
+    B.r = r; B.rpad = rpad; B.eps = c.eps;
+    B.F[0] = H[i]; B.F[1] = W[i];
+    B.ldf[0] = n; B.ldf[1] = r;
+    B.op_hi[0] = hop; B.op_lo[0] = hopl; B.ldop[0] = ld_n;
+    B.op_hi[1] = wop; B.op_lo[1] = wopl; B.ldop[1] = ld_p;
+    B.Gpad[0] = gwp; B.Gpad[1] = ghp;
+    B.nkbt[0] = (int)nkb_p; B.nkbt[1] = (int)nkb_n;
+    B.tmap = 8 * i;
+    B.plane = plane;
+    CUtensorMap* m = &maps[8 * (size_t)i];
+    // half 0 (H update): X = V^T (n x p), Y = W^T plane (K = p)
+    bool ok = map_blocked(&m[0], xh, bf, (int64_t)ceil_div(n, 128) * nkb_p) &&
+              map_plane(&m[2], wop, bf, p, r, ld_p, rpad);
+    if (prec == NMF_BF16X3)
+      ok = ok && map_blocked(&m[1], xhl, bf, (int64_t)ceil_div(n, 128) * nkb_p) &&
+           map_plane(&m[3], wopl, bf, p, r, ld_p, rpad);
+    else { m[1] = m[0]; m[3] = m[2]; }
+    // half 1 (W update): X = V (p x n), Y = H plane (K = n)
+    ok = ok && map_blocked(&m[4], xw, bf, (int64_t)ceil_div(p, 128) * nkb_n) &&
+         map_plane(&m[6], hop, bf, n, r, ld_n, rpad);
+    if (prec == NMF_BF16X3)
+      ok = ok && map_blocked(&m[5], xwl, bf, (int64_t)ceil_div(p, 128) * nkb_n) &&
+           map_plane(&m[7], hopl, bf, n, r, ld_n, rpad);
+    else { m[5] = m[4]; m[7] = m[6]; }
+    if (!ok) {
+      nmf_batched_destroy(b);
+      return bfail(nullptr, NMF_ECUDA, "tensor map encoding failed");
+    }
+    gram[0][i] = GramInst{W[i], 0, r, p, r, gw64, gwp};
+    gram[1][i] = GramInst{H[i], 1, n, n, r, gh64, ghp};
+  }
+  // device tables
+  if ((e = balloc(b, (void**)&b->d_inst, sizeof(BatchInst) * count)) != cudaSuccess ||
+      (e = balloc(b, (void**)&b->d_maps, sizeof(CUtensorMap) * maps.size())) != cudaSuccess ||
+      (e = balloc(b, (void**)&b->d_gram[0], sizeof(GramInst) * count)) != cudaSuccess ||
+      (e = balloc(b, (void**)&b->d_gram[1], sizeof(GramInst) * count)) != cudaSuccess)
+    return fail_cuda(e, "cudaMalloc");
+  cudaMemcpyAsync(b->d_inst, inst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, b->st);
+  cudaMemcpyAsync(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice, b->st);
+  cudaMemcpyAsync(b->d_gram[0], gram[0].data(), sizeof(GramInst) * count, cudaMemcpyHostToDevice, b->st);
+  cudaMemcpyAsync(b->d_gram[1], gram[1].data(), sizeof(GramInst) * count, cudaMemcpyHostToDevice, b->st);
+
+  // objective tables
+  std::vector<ObjInst> obj(count);
+  std::vector<int> tile_inst;
+  for (int i = 0; i < count; ++i) {
+    const int tn = (int)ceil_div(cfgs[i].n, 128);
+    const int tm = (int)ceil_div(cfgs[i].p, 64);
+    obj[i] = ObjInst{V[i], W[i], H[i], cfgs[i].p, cfgs[i].n, cfgs[i].r, (int)tile_inst.size(), tn};
+    for (int t = 0; t < tm * tn; ++t) tile_inst.push_back(i);
+  }
+  b->obj_tiles = (int)tile_inst.size();
+  if ((e = balloc(b, (void**)&b->d_obj, sizeof(ObjInst) * count)) != cudaSuccess ||
+      (e = balloc(b, (void**)&b->d_tile_inst, sizeof(int) * tile_inst.size())) != cudaSuccess ||
+      (e = balloc(b, (void**)&b->d_tile_part, sizeof(double) * tile_inst.size())) != cudaSuccess ||
+      (e = balloc(b, (void**)&b->d_f, sizeof(double) * count)) != cudaSuccess ||
+      (e = balloc(b, (void**)&b->d_err, sizeof(int))) != cudaSuccess)
+    return fail_cuda(e, "cudaMalloc");
+  cudaMemcpyAsync(b->d_obj, obj.data(), sizeof(ObjInst) * count, cudaMemcpyHostToDevice, b->st);
+  cudaMemcpyAsync(b->d_tile_inst, tile_inst.data(), sizeof(int) * tile_inst.size(),
+                  cudaMemcpyHostToDevice, b->st);
+  if ((e = cudaMallocHost((void**)&b->h_f, sizeof(double) * count)) != cudaSuccess ||
+      (e = cudaMallocHost((void**)&b->h_err, sizeof(int))) != cudaSuccess)
+    return fail_cuda(e, "cudaMallocHost");
+
+  // Work lists per half step, scheduled by the autotuner below.
+  std::vector<std::pair<int, int>> items[2];
+  std::vector<int> cost[2];
+  for (int i = 0; i < count; ++i) {
+    for (int h = 0; h < 2; ++h) {
+      const int tiles = (int)ceil_div(inst[i].M[h], 128);
+      for (int t = 0; t < tiles; ++t) {
+        items[h].push_back({i, t});
+        cost[h].push_back(inst[i].nkbt[h]);
+      }
+    }
+  }
+  // Candidate schedules: policy x grid; each is timed on one iteration (after
+  // a warm-up) and the fastest kept.  NMF_TUNE_CACHE (a file path) caches the
+  // choice per batch signature.
+  std::vector<std::pair<std::string, int>> cands;
+  for (const char* pol : {"lpt", "rr"})
+    for (int g : {b->sms, b->sms - b->sms / 8}) cands.push_back({pol, g});
+  std::string sig;
+  {
+    std::ostringstream os;
+    os << "prec" << (int)prec << "_sms" << b->sms << "_n" << count;
+    unsigned long long hsh = 1469598103934665603ull;
+    for (int i = 0; i < count; ++i) {
+      hsh = (hsh ^ (unsigned long long)cfgs[i].p) * 1099511628211ull;
+      hsh = (hsh ^ (unsigned long long)cfgs[i].n) * 1099511628211ull;
+      hsh = (hsh ^ (unsigned long long)cfgs[i].r) * 1099511628211ull;
+    }
+    os << "_" << std::hex << hsh;
+    sig = os.str();
+  }
+  const char* cache = std::getenv("NMF_TUNE_CACHE");
+  int chosen = -1;
+  if (cache) {
+    std::ifstream in(cache);
+    std::string k, pol;
+    int g;
+    while (in >> k >> pol >> g)
+      if (k == sig)
+        for (size_t c = 0; c < cands.size(); ++c)
+          if (cands[c].first == pol && cands[c].second == g) chosen = (int)c;
+  }
+  std::vector<int2> sched[2];
+  std::vector<int> off[2];
+  auto install = [&](int c) -> cudaError_t {
+    for (int h = 0; h < 2; ++h) {
+      make_schedule(items[h], cost[h], cands[c].second, cands[c].first, sched[h], off[h]);
+      b->grid[h] = cands[c].second;
+      if (!b->d_items[h]) {
+        cudaError_t e2 = balloc(b, (void**)&b->d_items[h], sizeof(int2) * sched[h].size());
+        if (e2 != cudaSuccess) return e2;
+        e2 = balloc(b, (void**)&b->d_off[h], sizeof(int) * (b->sms + 1));
+        if (e2 != cudaSuccess) return e2;
+      }
+      cudaMemcpyAsync(b->d_items[h], sched[h].data(), sizeof(int2) * sched[h].size(),
+                      cudaMemcpyHostToDevice, b->st);
+      cudaMemcpyAsync(b->d_off[h], off[h].data(), sizeof(int) * off[h].size(),
+                      cudaMemcpyHostToDevice, b->st);
+    }
+    b->schedule = cands[c].first + "/" + std::to_string(cands[c].second);
+    return cudaSuccess;
+  };
+  if (chosen < 0) {
+    // Tune on copies of the factors so that the caller's starting point is kept.
+    std::vector<float*> wsave(count), hsave(count);
+    for (int i = 0; i < count; ++i) {
+      const size_t wb = (size_t)cfgs[i].p * cfgs[i].r * 4, hb = (size_t)cfgs[i].r * cfgs[i].n * 4;
+      if ((e = balloc(b, (void**)&wsave[i], wb)) != cudaSuccess ||
+          (e = balloc(b, (void**)&hsave[i], hb)) != cudaSuccess)
+        return fail_cuda(e, "cudaMalloc");
+      cudaMemcpyAsync(wsave[i], W[i], wb, cudaMemcpyDeviceToDevice, b->st);
+      cudaMemcpyAsync(hsave[i], H[i], hb, cudaMemcpyDeviceToDevice, b->st);
+    }
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    double best = 1e300;
+    for (size_t c = 0; c < cands.size(); ++c) {
+      if ((e = install((int)c)) != cudaSuccess) return fail_cuda(e, "schedule");
+      if ((e = run_iteration(b)) != cudaSuccess) return fail_cuda(e, "tune");
+      cudaEventRecord(t0, b->st);
+      for (int rep = 0; rep < 2; ++rep)
+        if ((e = run_iteration(b)) != cudaSuccess) return fail_cuda(e, "tune");
+      cudaEventRecord(t1, b->st);
+      cudaEventSynchronize(t1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, t0, t1);
+      if (ms < best) { best = ms; chosen = (int)c; }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    // restore the starting factors and their planes
+    for (int i = 0; i < count; ++i) {
+      const size_t wb = (size_t)cfgs[i].p * cfgs[i].r * 4, hb = (size_t)cfgs[i].r * cfgs[i].n * 4;
+      cudaMemcpyAsync(W[i], wsave[i], wb, cudaMemcpyDeviceToDevice, b->st);
+      cudaMemcpyAsync(H[i], hsave[i], hb, cudaMemcpyDeviceToDevice, b->st);
+      const BatchInst& B = inst[i];
+      launch_factor_planes(W[i], kFactorRowMajor, cfgs[i].p, cfgs[i].r, cfgs[i].r, B.op_hi[1],
+                           B.op_lo[1], B.ldop[1], plane, b->st);
+      launch_factor_planes(H[i], kFactorColMajor, cfgs[i].n, cfgs[i].n, cfgs[i].r, B.op_hi[0],
+                           B.op_lo[0], B.ldop[0], plane, b->st);
+      count_launches(2);
+    }
+    if (cache) {
+      std::ofstream o(cache, std::ios::app);
+      o << sig << " " << cands[chosen].first << " " << cands[chosen].second << "\n";
+    }
+  }
+  if ((e = install(chosen)) != cudaSuccess) return fail_cuda(e, "schedule");
+  // One MM iteration of the whole batch as a CUDA graph, replayed per step.
+  cudaStream_t cap;
+  if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess)
+    return fail_cuda(e, "stream");
+  cudaStreamSynchronize(b->st);
+  cudaGraph_t gr = nullptr;
+  cudaStream_t saved = b->st;
+  b->st = cap;
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = run_iteration(b);
+    e = cudaStreamEndCapture(cap, &gr);
+    if (e1 != cudaSuccess) e = e1;
+  }
+  b->st = saved;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, gr, 0);
+  if (gr) cudaGraphDestroy(gr);
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess) return fail_cuda(e, "graph capture");
+  *out = b;
+  return NMF_OK;
+}
+
+nmf_status nmf_batched_step(nmf_batch* b, int iters) {
+  if (!b || iters < 0) return bfail(b, NMF_EINVAL, "bad arguments to nmf_batched_step");
+  for (int it = 0; it < iters; ++it) {
+    cudaError_t e = cudaGraphLaunch(b->graph, b->st);
+    if (e != cudaSuccess) return bfail(b, NMF_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    count_launches(2 * (1 + 1));
+  }
+  return NMF_OK;
+}
+
+nmf_status nmf_batched_objective(nmf_batch* b, double* f_out) {
+  if (!b || !f_out) return bfail(b, NMF_EINVAL, "bad arguments to nmf_batched_objective");
+  const int grid = b->obj_tiles < 152 * 8 ? b->obj_tiles : 152 * 8;
+  k_batched_objective<<<grid, 256, 0, b->st>>>(b->d_obj, b->count, b->d_tile_inst, b->obj_tiles,
+                                               b->d_tile_part);
+  k_batched_obj_sum<<<(b->count + 127) / 128, 128, 0, b->st>>>(b->d_obj, b->count, b->d_tile_part,
+                                                               b->d_f);
+  count_launches(2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return bfail(b, NMF_ECUDA, std::string("objective: ") + cudaGetErrorString(e));
+  cudaMemcpyAsync(b->h_f, b->d_f, sizeof(double) * b->count, cudaMemcpyDeviceToHost, b->st);
+  cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->st);
+  if ((e = cudaStreamSynchronize(b->st)) != cudaSuccess)
+    return bfail(b, NMF_ECUDA, std::string("sync: ") + cudaGetErrorString(e));
+  if (*b->h_err) {
+    cudaMemsetAsync(b->d_err, 0, sizeof(int), b->st);
+    return bfail(b, NMF_ETIMEOUT, "a bounded device wait expired; results are invalid");
+  }
+  std::memcpy(f_out, b->h_f, sizeof(double) * b->count);
+  return NMF_OK;
+}
+
+void nmf_batched_destroy(nmf_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->st);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (void* p : b->allocs) cudaFree(p);
+  if (b->h_f) cudaFreeHost(b->h_f);
+  if (b->h_err) cudaFreeHost(b->h_err);
+  (void)cudaGetLastError();
+  delete b;
+}
+
+}  // extern "C"

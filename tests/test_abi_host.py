@@ -89,3 +89,27 @@ def test_null_pointers_rejected(lib):
     assert lib.nmf_objective(None, None) == nmf.EINVAL
     assert lib.nmf_half_step(None, 0) == nmf.EINVAL
     lib.nmf_destroy(None)  # no-op
+
+
+def test_batched_rejections_on_the_host(lib):
+    from paper_1003_3272_gb300 import nmf
+    cfgs = (nmf.Config * 2)()
+    for i in range(2):
+        lib.nmf_config_default(ctypes.byref(cfgs[i]), 100, 120, 10)
+        cfgs[i].prec = nmf.BF16X3
+    ptrs = (ctypes.c_void_p * 2)(16, 16)
+    out = ctypes.c_void_p(123)
+    # a rank above the grouped kernel's 32
+    cfgs[1].r = 40
+    assert lib.nmf_batched_init(2, cfgs, ptrs, ptrs, ptrs, None, ctypes.byref(out)) == nmf.EINVAL
+    assert out.value is None
+    cfgs[1].r = 10
+    # mixed precisions
+    cfgs[1].prec = nmf.TF32
+    assert lib.nmf_batched_init(2, cfgs, ptrs, ptrs, ptrs, None, ctypes.byref(out)) == nmf.EINVAL
+    # the float32 form is not a grouped tensor-core launch
+    for i in range(2):
+        cfgs[i].prec = nmf.FP32
+    assert lib.nmf_batched_init(2, cfgs, ptrs, ptrs, ptrs, None, ctypes.byref(out)) == nmf.EUNSUPPORTED
+    assert lib.nmf_batched_init(0, cfgs, ptrs, ptrs, ptrs, None, ctypes.byref(out)) == nmf.EINVAL
+    assert lib.nmf_batched_step(None, 1) == nmf.EINVAL
