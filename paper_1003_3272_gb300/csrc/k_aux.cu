@@ -91,7 +91,8 @@ __global__ void k_split_bf16(const float* __restrict__ src, int64_t rows, int64_
 // 128 rows x KBE columns (KBE = 64 bf16 or 32 tf32 = 128 bytes); block
 // (mt, kb) is stored contiguously (row pitch 128 bytes) at block index
 // mt * nkb + kb, so one tile's K range is a single contiguous stream.
-// mode 0: bf16 hi (and lo = bf16(v - hi) when lo != null); mode 1: tf32.
+// mode 0: bf16 hi (and lo = bf16(v - hi) when lo != null); mode 1: tf32;
+// mode 2: float32 as is.
 // Entries outside M x K are never written (the buffer starts zeroed).
 __global__ void k_operand_blocked(const float* __restrict__ src, int64_t rows, int64_t cols,
                                   int64_t lds, int transpose, int mode, void* __restrict__ hi,
@@ -113,6 +114,8 @@ __global__ void k_operand_blocked(const float* __restrict__ src, int64_t rows, i
     const int64_t off = (((m >> 7) * nkb + k / kbe) * 128 + (m & 127)) * kbe + (k % kbe);
     if (mode == 1) {
       static_cast<float*>(hi)[off] = round_tf32(v);
+    } else if (mode == 2) {
+      static_cast<float*>(hi)[off] = v;
     } else {
       const __nv_bfloat16 h = __float2bfloat16_rn(v);
       static_cast<__nv_bfloat16*>(hi)[off] = h;
@@ -375,11 +378,11 @@ cudaError_t launch_split_bf16(const float* src, int64_t rows, int64_t cols, int6
 }
 
 cudaError_t launch_operand_blocked(const float* src, int64_t rows, int64_t cols, int64_t lds,
-                                   bool transpose, bool tf32, void* hi, void* lo, int64_t nkb,
+                                   bool transpose, int mode, void* hi, void* lo, int64_t nkb,
                                    int kbe, cudaStream_t st) {
   dim3 grid((unsigned)ceil_div(cols, 32), (unsigned)ceil_div(rows, 32));
-  k_operand_blocked<<<grid, dim3(32, 8), 0, st>>>(src, rows, cols, lds, transpose ? 1 : 0,
-                                                   tf32 ? 1 : 0, hi, lo, nkb, kbe);
+  k_operand_blocked<<<grid, dim3(32, 8), 0, st>>>(src, rows, cols, lds, transpose ? 1 : 0, mode,
+                                                   hi, lo, nkb, kbe);
   return cudaGetLastError();
 }
 

@@ -677,8 +677,8 @@ nmf_status nmf_batched_init(int count, const nmf_config* cfgs, const float* cons
     if ((e = balloc(b, (void**)&gwp, (size_t)kBR * kBR * 4)) != cudaSuccess) return fail_cuda(e, "cudaMalloc");
     if ((e = balloc(b, (void**)&ghp, (size_t)kBR * kBR * 4)) != cudaSuccess) return fail_cuda(e, "cudaMalloc");
     // operand copies of V and planes of the starting factors
-    if ((e = launch_operand_blocked(V[i], p, n, n, false, !bf, xw, xwl, nkb_n, kbe, b->st)) != cudaSuccess ||
-        (e = launch_operand_blocked(V[i], p, n, n, true, !bf, xh, xhl, nkb_p, kbe, b->st)) != cudaSuccess ||
+    if ((e = launch_operand_blocked(V[i], p, n, n, false, bf ? 0 : 1, xw, xwl, nkb_n, kbe, b->st)) != cudaSuccess ||
+        (e = launch_operand_blocked(V[i], p, n, n, true, bf ? 0 : 1, xh, xhl, nkb_p, kbe, b->st)) != cudaSuccess ||
         (e = launch_factor_planes(W[i], kFactorRowMajor, p, r, r, wop, wopl, ld_p, plane, b->st)) != cudaSuccess ||
         (e = launch_factor_planes(H[i], kFactorColMajor, n, n, r, hop, hopl, ld_n, plane, b->st)) != cudaSuccess)
       return fail_cuda(e, "prepare");

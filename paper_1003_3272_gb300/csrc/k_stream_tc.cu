@@ -486,10 +486,10 @@ cudaError_t prepare_kernel(void* fn, int smem) {
   return cudaSuccess;
 }
 
-int max_clusters(void* fn, int smem, int S, int sms) {
+int max_clusters(void* fn, int smem, int threads, int S, int sms) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)((sms / S) * S), 1, 1);
-  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
   cfg.dynamicSmemBytes = (size_t)smem;
   cudaLaunchAttribute attr;
   attr.id = cudaLaunchAttributeClusterDimension;
@@ -513,15 +513,19 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
                    int user_split, TcPlan* plan, std::string* err) {
   TcPlan& pl = *plan;
   pl.prec = prec;
-  pl.rpad = rank_pad16(r);
+  // float32 FMA path: ranks padded to 8; tensor cores: N granularity 16
+  pl.rpad = prec == NMF_FP32 ? (int)round_up(r, 8) : rank_pad16(r);
   pl.block_m = kBM;
-  pl.kblock = (prec == NMF_TF32) ? 32 : 64;
+  pl.kblock = (prec == NMF_TF32 || prec == NMF_FP32) ? 32 : 64;
   pl.M = M; pl.K = K; pl.r = r;
   pl.tiles = (int)ceil_div(M, kBM);
   if (M > INT32_MAX || K > INT32_MAX) { if (err) *err = "size exceeds TMA coordinates"; return NMF_EINVAL; }
   void* fn = nullptr;
-  int smem = 0;
-  if (!kernel_for(prec, pl.rpad, &fn, &smem)) { if (err) *err = "no kernel for this rank"; return NMF_EINVAL; }
+  int smem = 0, threads = kThreads;
+  const bool have = prec == NMF_FP32 ? f32_kernel_for(pl.rpad, &fn, &smem, &threads)
+                                     : kernel_for(prec, pl.rpad, &fn, &smem);
+  if (!have) { if (err) *err = "no kernel for this rank"; return NMF_EINVAL; }
+  pl.threads = threads;
   if (prepare_kernel(fn, smem) != cudaSuccess) {
     (void)cudaGetLastError();
     if (err) *err = "cannot configure the tensor-core kernel's shared memory";
@@ -545,7 +549,7 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
   for (int S = 2; S <= 8; S *= 2) {
     if (want > 0 && S != want) continue;
     if (S > 2 && nkb < (int64_t)S) continue;
-    const int maxc = max_clusters(fn, smem, S, sms);
+    const int maxc = max_clusters(fn, smem, threads, S, sms);
     if (maxc < 1) continue;
     const int G = maxc < pl.tiles ? maxc : pl.tiles;
     const int rounds = (int)ceil_div(pl.tiles, G);
@@ -568,7 +572,7 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
   pl.kchunk = ceil_div(nkb, bestS) * pl.kblock;
   pl.grid = bestG * bestS;
   pl.fn = fn;
-  const bool bf = prec != NMF_TF32;
+  const bool bf = prec == NMF_BF16X3 || prec == NMF_BF16;
   (void)ldx;
   pl.nkbt = (int)nkb;
   const int64_t nblocks = (int64_t)pl.tiles * nkb;
@@ -586,6 +590,7 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
 
 cudaError_t tc_launch(const TcPlan& pl, const EpiArgs& ep, const TcGram& gr, int* err,
                       cudaStream_t st) {
+  if (pl.prec == NMF_FP32) return f32_launch(pl, ep, gr, err, st);
   TcParams prm;
   prm.M = pl.M; prm.K = pl.K; prm.r = pl.r;
   prm.S = pl.S; prm.tiles = pl.tiles; prm.nclusters = pl.nclusters; prm.kper = pl.kchunk;

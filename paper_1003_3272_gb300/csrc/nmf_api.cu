@@ -93,9 +93,6 @@ struct nmf_ctx {
   unsigned long long gctr_host = 0;       // its value after every launch so far
   float* GWpad = nullptr; float* GHpad = nullptr;   // rpad x rpad Grams (tensor-core form)
   double* tc_gpart = nullptr;             // tensor-core prologue partials (one per block)
-  // split-K
-  float* part = nullptr;
-  unsigned* counters = nullptr;
   // objective
   double* obj_parts = nullptr;
   double* f_dev = nullptr;
@@ -189,23 +186,6 @@ void prof_collect(nmf_ctx* c) {
   c->ev_open.clear();
 }
 
-// Split-K plan: about `waves` resident blocks per SM over tiles x splits.
-void plan_split(HalfPlan& h, int block_m, int kblock, int sms, int waves, int user_split) {
-  h.tiles = (int)ceil_div(h.M, block_m);
-  int splits;
-  if (user_split > 0) {
-    splits = user_split;
-  } else {
-    const int64_t want = (int64_t)sms * waves;
-    splits = (int)ceil_div(want, h.tiles);
-    const int64_t max_by_k = ceil_div(h.K, (int64_t)kblock * 4);  // >= 4 k-blocks per split
-    if (splits > max_by_k) splits = (int)max_by_k;
-    if (splits < 1) splits = 1;
-  }
-  h.kchunk = round_up(ceil_div(h.K, splits), kblock);
-  h.splits = (int)ceil_div(h.K, h.kchunk);
-}
-
 nmf_status validate_cfg(const nmf_config* cfg) {
   if (!cfg) { set_err(nullptr, "cfg is NULL"); return NMF_EINVAL; }
   if (cfg->p < 1 || cfg->n < 1) { set_err(nullptr, "p and n must be >= 1"); return NMF_EINVAL; }
@@ -238,20 +218,13 @@ nmf_status prepare(nmf_ctx* c, bool seed_factors, uint64_t seed) {
   const int r = c->r;
   cudaStream_t st = c->st;
   ProfScope ps(c, 3);
-  if (c->plane == kPlaneF32) {
-    if (c->Xw_hi != c->V) {
-      CK(launch_copy_pad(c->V, p, n, n, (float*)c->Xw_hi, c->ld_n, false, st), "copy V");
-      launched(1);
-    }
-    CK(launch_transpose_pad(c->V, p, n, n, (float*)c->Xh_hi, c->ld_p, false, st), "transpose V");
-    launched(1);
-  } else {
+  {
     // tile-blocked copies: Xw = V (p x n), Xh = V^T (n x p)
-    const bool t32 = c->plane == kPlaneTF32;
-    const int kbe = t32 ? 32 : 64;
-    CK(launch_operand_blocked(c->V, p, n, n, false, t32, (void*)c->Xw_hi, (void*)c->Xw_lo,
+    const int mode = c->plane == kPlaneTF32 ? 1 : (c->plane == kPlaneF32 ? 2 : 0);
+    const int kbe = mode == 0 ? 64 : 32;
+    CK(launch_operand_blocked(c->V, p, n, n, false, mode, (void*)c->Xw_hi, (void*)c->Xw_lo,
                               ceil_div(n, kbe), kbe, st), "operand V");
-    CK(launch_operand_blocked(c->V, p, n, n, true, t32, (void*)c->Xh_hi, (void*)c->Xh_lo,
+    CK(launch_operand_blocked(c->V, p, n, n, true, mode, (void*)c->Xh_hi, (void*)c->Xh_lo,
                               ceil_div(p, kbe), kbe, st), "operand V^T");
     launched(2);
   }
@@ -278,17 +251,16 @@ nmf_status build_ctx(nmf_ctx* c) {
   const int64_t p = c->p, n = c->n;
   const int r = c->r;
   const nmf_precision prec = c->cfg.prec;
-  const bool tc = prec != NMF_FP32;
   cudaStream_t st = c->st;
   int dev = 0;
   CK(cudaGetDevice(&dev), "cudaGetDevice");
   CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev), "attr");
-  if (tc) {
+  {
     int major = 0, minor = 0;
     CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev), "attr");
     CK(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev), "attr");
     if (major != 10 || minor != 3) {
-      set_err(&c->err, "tensor-core precisions need an sm_103 GPU (found sm_%d%d)", major, minor);
+      set_err(&c->err, "the streaming kernels need an sm_103 GPU (found sm_%d%d)", major, minor);
       return NMF_EUNSUPPORTED;
     }
   }
@@ -314,21 +286,10 @@ nmf_status build_ctx(nmf_ctx* c) {
   c->ld_p = round_up(p, align_el);
   c->plane = (prec == NMF_BF16X3) ? kPlaneBF16x2
              : (prec == NMF_BF16) ? kPlaneBF16 : (prec == NMF_TF32 ? kPlaneTF32 : kPlaneF32);
-  c->rpad = tc ? rank_pad16(r) : (int)round_up(r, 8);
-  if (prec == NMF_FP32) {
-    if (n == c->ld_n && is_aligned16(c->V)) {
-      c->Xw_hi = c->V;
-    } else {
-      float* d;
-      if ((s = dalloc(c, (void**)&d, (size_t)p * c->ld_n * 4)) != NMF_OK) return s;
-      c->Xw_hi = d;
-    }
-    float* t;
-    if ((s = dalloc(c, (void**)&t, (size_t)n * c->ld_p * 4)) != NMF_OK) return s;
-    c->Xh_hi = t;
-  } else {
+  c->rpad = prec == NMF_FP32 ? (int)round_up(r, 8) : rank_pad16(r);
+  {
     // tile-blocked copies (128 rows x 128 bytes per block), zero padded
-    const int kbe = prec == NMF_TF32 ? 32 : 64;
+    const int kbe = bf ? 64 : 32;
     const size_t bw = (size_t)ceil_div(p, 128) * ceil_div(n, kbe) * 128 * 128;  // bytes
     const size_t bh = (size_t)ceil_div(n, 128) * ceil_div(p, kbe) * 128 * 128;
     void *a = nullptr, *b = nullptr, *ta = nullptr, *tb = nullptr;
@@ -376,42 +337,24 @@ nmf_status build_ctx(nmf_ctx* c) {
   hw.ep.op_hi = c->Wop_hi; hw.ep.op_lo = c->Wop_lo; hw.ep.ldop = c->ld_p;
   hw.ep.G = c->GH32; hw.G32_out = c->GW32; hw.G64_out = c->GW64; hw.own = 0;
 
-  size_t part_floats = 0, counters = 0;
-  size_t gtiles[2] = {(size_t)ceil_div(p, 128), (size_t)ceil_div(n, 128)};
+  const size_t gtiles[2] = {(size_t)ceil_div(p, 128), (size_t)ceil_div(n, 128)};
   for (HalfPlan* h : {&hh, &hw}) {
     h->ep.r = r;
     h->ep.eps = c->cfg.eps;
     h->ep.plane = c->plane;
-    int bm;
-    if (!tc) {
-      bm = simt_block_m(r);
-      plan_split(*h, bm, 32, c->sms, 4, c->cfg.split_k);
-    } else {
-      s = tc_plan(c->cfg.prec, h->X_hi, h->X_lo, h->ldx, h->Y_hi, h->Y_lo, h->ldy, h->M, h->K, r,
-                  c->sms, c->cfg.split_k, &h->tc, &c->err);
-      if (s != NMF_OK) return s;
-      bm = h->tc.block_m;
-      h->tiles = h->tc.tiles;
-      h->splits = h->tc.splits;
-      h->kchunk = h->tc.kchunk;
-    }
-    if (!tc && h->splits > 1) {
-      const size_t pf = (size_t)h->tiles * h->splits * bm * round_up(r, 8);
-      if (pf > part_floats) part_floats = pf;
-    }
-    if ((size_t)h->tiles > counters) counters = h->tiles;
-    // partial Grams this half produces: one per tile (fp32 form) or per
-    // tile row slice (tensor-core form)
-    const size_t np = tc ? (size_t)h->tiles * h->tc.S : (size_t)h->tiles;
-    if (np > gtiles[h->own]) gtiles[h->own] = np;
+    s = tc_plan(c->cfg.prec, h->X_hi, h->X_lo, h->ldx, h->Y_hi, h->Y_lo, h->ldy, h->M, h->K, r,
+                c->sms, c->cfg.split_k, &h->tc, &c->err);
+    if (s != NMF_OK) return s;
+    h->tiles = h->tc.tiles;
+    h->splits = h->tc.splits;
+    h->kchunk = h->tc.kchunk;
   }
-  if ((s = dalloc(c, (void**)&c->part, part_floats * 4)) != NMF_OK) return s;
-  if ((s = dalloc(c, (void**)&c->counters, counters * 4)) != NMF_OK) return s;
+  // partial Grams of the starting factors (and of nmf_read_gram): per 128 rows
   for (int f = 0; f < 2; ++f)
     if ((s = dalloc(c, (void**)&c->gpart[f], gtiles[f] * rr * 4)) != NMF_OK) return s;
   if ((s = dalloc(c, (void**)&c->gctr, sizeof(unsigned long long))) != NMF_OK) return s;
   c->gctr_host = 0;
-  if (tc) {
+  {
     const size_t rp2 = (size_t)c->rpad * c->rpad;
     if ((s = dalloc(c, (void**)&c->GWpad, rp2 * 4)) != NMF_OK) return s;
     if ((s = dalloc(c, (void**)&c->GHpad, rp2 * 4)) != NMF_OK) return s;
@@ -458,21 +401,8 @@ nmf_status check_device_error(nmf_ctx* c) {
 nmf_status run_half(nmf_ctx* c, int which) {
   HalfPlan& h = c->half[which];
   const int own = h.own, other = 1 - h.own;
-  if (c->cfg.prec == NMF_FP32) {
-    SplitArgs sp{c->part, c->counters, h.splits, h.kchunk};
-    {
-      ProfScope ps(c, 0);
-      CK(launch_stream_simt(static_cast<const float*>(h.X_hi), h.ldx,
-                            static_cast<const float*>(h.Y_hi), h.ldy, h.M, h.K, c->r, sp, h.ep,
-                            c->st), "stream (fp32)");
-      launched(1);
-    }
-    c->gcount[own] = h.tiles;
-    ProfScope ps(c, 1);
-    CK(launch_gram_reduce(c->gpart[own], c->gcount[own], c->r, h.G32_out, h.G64_out, c->st),
-       "gram reduce");
-    launched(1);
-  } else {
+  (void)own;
+  {
     // The launch forms the other factor's Gram itself (prologue), then
     // streams V and updates this factor.
     TcGram g;
@@ -555,8 +485,8 @@ nmf_status nmf_step(nmf_ctx* c, int iters) {
   if (!c) { set_err(nullptr, "ctx is NULL"); return NMF_EINVAL; }
   if (iters < 0) { set_err(&c->err, "iters must be >= 0"); return NMF_EINVAL; }
   const int first = c->cfg.order == NMF_ORDER_H_FIRST ? 0 : 1;
-  const bool tc = c->cfg.prec != NMF_FP32;
-  // tensor-core launches chain by programmatic dependent launch: one bracket
+  const bool tc = true;
+  // the streaming launches chain by programmatic dependent launch: one bracket
   ProfScope ps(c, 0, tc ? 2 * iters : 0);
   c->in_step = tc;
   nmf_status s = NMF_OK;

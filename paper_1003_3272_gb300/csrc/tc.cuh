@@ -22,6 +22,7 @@ struct TcPlan {
   int grid = 0;
   int smem = 0;
   int S = 1;             // cluster size (K-splits per tile)
+  int threads = 256;     // block size of the kernel instance
   int nkbt = 0;          // k-blocks per tile row of the blocked X copy
   int nclusters = 0;     // persistent clusters
   void* fn = nullptr;    // kernel instance
@@ -48,5 +49,10 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
 
 cudaError_t tc_launch(const TcPlan& plan, const EpiArgs& ep, const TcGram& gram, int* err,
                       cudaStream_t st);
+
+// The float32 FMA form of the same half step (k_stream_f32.cu).
+bool f32_kernel_for(int rpad, void** fn, int* smem, int* threads);
+cudaError_t f32_launch(const TcPlan& plan, const EpiArgs& ep, const TcGram& gram, int* err,
+                       cudaStream_t st);
 
 }  // namespace nmf

@@ -39,31 +39,43 @@ __host__ __device__ constexpr int dedicated_floats() {
 
 // Denominators of one helper thread: ranks kg*8 .. kg*8+7 of up to 8 rows
 // mg, mg + MG, ... of the slice (thread h: kg = h % KG, mg = h / KG).
-template <int RPAD>
+template <int RPAD, int NH = kHelpers>
 struct DenTile {
   static constexpr int KG = RPAD / 8;
-  static constexpr int MG = kHelpers / KG;
-  float d[2][4][8];
+  static constexpr int MG = NH / KG;
+  static constexpr int NA = (kRmax + 4 * MG - 1) / (4 * MG);   // passes of 4 rows
+  float d[NA][4][8];
+  // Threads that hold no denominators call this at the end of their own
+  // work, so that the registers are not live across it.
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) d[a][i][j] = 0.f;
+  }
 };
 
+template <int NH = kHelpers>
 __device__ __forceinline__ void helper_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kHelpers) : "memory");
+  asm volatile("bar.sync 1, %0;" ::"n"(NH) : "memory");
 }
 
 // Values of rows [m0, m0 + nrows) (nrows <= kQsRows) of a factor, in the
 // order they land in Qs[row][k] (zero for k >= r and rows beyond nrows):
 // each thread owns up to SV values and issues all their loads at once.
 // layout 0: F[m * ldf + k];  layout 1: F[k * ldf + m].
-template <int RPAD>
+template <int RPAD, int NH = kHelpers>
 struct RowStage {
   static constexpr int N = kQsRows * RPAD;
-  static constexpr int SV = (N + kHelpers - 1) / kHelpers;
+  static constexpr int SV = (N + NH - 1) / NH;
   float v[SV];
   __device__ __forceinline__ void load(const float* F, int layout, int64_t ldf, int r,
                                        int64_t m0, int nrows, int h) {
 #pragma unroll
     for (int j = 0; j < SV; ++j) {
-      const int i = h + j * kHelpers;
+      const int i = h + j * NH;
       int row, k;
       if (layout == 0) { row = i / RPAD; k = i % RPAD; }
       else             { k = i / kQsRows; row = i % kQsRows; }
@@ -76,7 +88,7 @@ struct RowStage {
     constexpr int LQ = ldq<RPAD>();
 #pragma unroll
     for (int j = 0; j < SV; ++j) {
-      const int i = h + j * kHelpers;
+      const int i = h + j * NH;
       if (i < N) {
         int row, k;
         if (layout == 0) { row = i / RPAD; k = i % RPAD; }
@@ -89,81 +101,71 @@ struct RowStage {
 
 // Partial Gram of rows [q0, q1) of Q, written to gpart (r x r doubles, both
 // triangles): float32 sums over windows of 128 rows, float64 across
-// windows.  Rows are staged 32 at a time; the next 32 are loaded into
-// registers while the current ones are multiplied.
-template <int RPAD>
+// windows.  Each thread owns one 4 x 4 block (kb <= lb) per pass over the
+// rows (passes until every block is done); rows are staged 32 at a time,
+// the next 32 loaded into registers while the current ones are multiplied.
+template <int RPAD, int NH = kHelpers>
 __device__ void gram_rows(float* Qs, const float* Q, int layout, int64_t ldq_g, int64_t q0,
                           int64_t q1, int r, double* gpart, int h) {
   constexpr int LQ = ldq<RPAD>();
-  constexpr int NBMAX = RPAD / 4;
-  constexpr int MAXB = (NBMAX * (NBMAX + 1) / 2 + kHelpers - 1) / kHelpers;
   const int nbr = (r + 3) / 4;
   const int npairs = nbr * (nbr + 1) / 2;
-  int kb[MAXB], lb[MAXB];
-#pragma unroll
-  for (int t = 0; t < MAXB; ++t) {
-    const int it = h + t * kHelpers;
-    int a = 0, rem = it < npairs ? it : 0;
-    while (rem >= nbr - a) { rem -= nbr - a; ++a; }
-    kb[t] = a;
-    lb[t] = a + rem;
-  }
-  float acc[MAXB][4][4];
-  double tot[MAXB][4][4];
-#pragma unroll
-  for (int t = 0; t < MAXB; ++t)
+  for (int pb = 0; pb < npairs; pb += NH) {
+    const int it = pb + h;
+    const bool mine = it < npairs;
+    int kb = 0, rem = mine ? it : 0;
+    while (rem >= nbr - kb) { rem -= nbr - kb; ++kb; }
+    const int lb = kb + rem;
+    float acc[4][4];
+    double tot[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) { acc[t][i][j] = 0.f; tot[t][i][j] = 0.0; }
-  RowStage<RPAD> st;
-  if (q0 < q1) st.load(Q, layout, ldq_g, r, q0, (int)min((int64_t)kQsRows, q1 - q0), h);
-  int in_window = 0;
-  for (int64_t s0 = q0; s0 < q1; s0 += kQsRows) {
-    helper_sync();              // previous rows consumed
-    st.store(Qs, layout, h);
-    helper_sync();
-    const int64_t s1 = s0 + kQsRows;
-    if (s1 < q1) st.load(Q, layout, ldq_g, r, s1, (int)min((int64_t)kQsRows, q1 - s1), h);
-#pragma unroll
-    for (int t = 0; t < MAXB; ++t) {
-      if (h + t * kHelpers >= npairs) continue;
+      for (int j = 0; j < 4; ++j) { acc[i][j] = 0.f; tot[i][j] = 0.0; }
+    RowStage<RPAD, NH> st;
+    if (q0 < q1) st.load(Q, layout, ldq_g, r, q0, (int)min((int64_t)kQsRows, q1 - q0), h);
+    int in_window = 0;
+    for (int64_t s0 = q0; s0 < q1; s0 += kQsRows) {
+      helper_sync<NH>();          // previous rows consumed
+      st.store(Qs, layout, h);
+      helper_sync<NH>();
+      const int64_t s1 = s0 + kQsRows;
+      if (s1 < q1) st.load(Q, layout, ldq_g, r, s1, (int)min((int64_t)kQsRows, q1 - s1), h);
+      if (mine) {
 #pragma unroll 4
-      for (int m = 0; m < kQsRows; ++m) {
-        const float4 a = *reinterpret_cast<const float4*>(&Qs[m * LQ + kb[t] * 4]);
-        const float4 b = *reinterpret_cast<const float4*>(&Qs[m * LQ + lb[t] * 4]);
-        const float av[4] = {a.x, a.y, a.z, a.w};
-        const float bv[4] = {b.x, b.y, b.z, b.w};
+        for (int m = 0; m < kQsRows; ++m) {
+          const float4 a = *reinterpret_cast<const float4*>(&Qs[m * LQ + kb * 4]);
+          const float4 b = *reinterpret_cast<const float4*>(&Qs[m * LQ + lb * 4]);
+          const float av[4] = {a.x, a.y, a.z, a.w};
+          const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[t][i][j] = fmaf(av[i], bv[j], acc[t][i][j]);
-      }
-    }
-    in_window += kQsRows;
-    if (in_window == 128 || s1 >= q1) {   // fold the window into float64
-#pragma unroll
-      for (int t = 0; t < MAXB; ++t)
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) { tot[t][i][j] += (double)acc[t][i][j]; acc[t][i][j] = 0.f; }
-      in_window = 0;
-    }
-  }
-#pragma unroll
-  for (int t = 0; t < MAXB; ++t) {
-    if (h + t * kHelpers >= npairs) continue;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int k = kb[t] * 4 + i, l = lb[t] * 4 + j;
-        if (k < r && l < r) {
-          gpart[k * r + l] = tot[t][i][j];
-          gpart[l * r + k] = tot[t][i][j];
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
         }
       }
+      in_window += kQsRows;
+      if (in_window == 128 || s1 >= q1) {   // fold the window into float64
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) { tot[i][j] += (double)acc[i][j]; acc[i][j] = 0.f; }
+        in_window = 0;
+      }
+    }
+    if (mine) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int k = kb * 4 + i, l = lb * 4 + j;
+          if (k < r && l < r) {
+            gpart[k * r + l] = tot[i][j];
+            gpart[l * r + k] = tot[i][j];
+          }
+        }
+    }
+    helper_sync<NH>();            // Qs free for the next pass
   }
 }
 
@@ -172,15 +174,15 @@ __device__ void gram_rows(float* Qs, const float* Q, int layout, int64_t ldq_g, 
 // (g = h / ne, ng = 192 / ne groups); the group sums are then added in
 // group order.  Writes G64 (r x r) and the zero-padded float32 copy Gpad.
 // `scratch` holds 192 doubles (shared).
-template <int RPAD>
+template <int RPAD, int NH = kHelpers>
 __device__ void gram_reduce_slice(const double* gpart, int nparts, int r, int e0, int e1,
                                   double* G64, float* Gpad, double* scratch, int h) {
   const int rr = r * r;
   const int ne = e1 - e0;
   if (ne <= 0) return;
-  for (int eb = e0; eb < e1; eb += kHelpers) {
-    const int nb = min(kHelpers, e1 - eb);
-    const int ng = kHelpers / nb;
+  for (int eb = e0; eb < e1; eb += NH) {
+    const int nb = min(NH, e1 - eb);
+    const int ng = NH / nb;
     const int g = h / nb, e = eb + h % nb;
     double s = 0.0;
     if (g < ng) {
@@ -197,43 +199,45 @@ __device__ void gram_reduce_slice(const double* gpart, int nparts, int r, int e0
       }
       scratch[g * nb + (h % nb)] = s;
     }
-    helper_sync();
+    helper_sync<NH>();
     if (h < nb) {
       double tot = 0.0;
       for (int gg = 0; gg < ng; ++gg) tot += scratch[gg * nb + h];
       G64[eb + h] = tot;
       Gpad[((eb + h) / r) * RPAD + ((eb + h) % r)] = (float)tot;
     }
-    helper_sync();
+    helper_sync<NH>();
   }
 }
 
 // Old rows of the slice into Os (issued early: they do not depend on G).
-template <int RPAD>
+template <int RPAD, int NH = kHelpers>
 __device__ void load_old(float* Os, const EpiArgs& e, int R, int64_t row0, int rows, int h) {
   constexpr int LO = ldo<RPAD>();
-  constexpr int NV = (kRmax * RPAD + kHelpers - 1) / kHelpers;
+  constexpr int NV = 16;   // loads in flight per thread per batch
   const int r = e.r;
-  float v[NV];
+  for (int b0 = 0; b0 < R * RPAD; b0 += NV * NH) {
+    float v[NV];
 #pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    const int i = h + j * kHelpers;
-    int m, k;
-    if (e.layout == kFactorRowMajor) { m = i / RPAD; k = i % RPAD; }
-    else                             { k = i / R;    m = i % R; }
-    v[j] = (i < R * RPAD && m < rows && k < r)
-               ? (e.layout == kFactorRowMajor ? e.F[(row0 + m) * r + k]
-                                              : e.F[(int64_t)k * e.ldf + row0 + m])
-               : 0.f;
-  }
-#pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    const int i = h + j * kHelpers;
-    if (i < R * RPAD) {
+    for (int j = 0; j < NV; ++j) {
+      const int i = b0 + h + j * NH;
       int m, k;
       if (e.layout == kFactorRowMajor) { m = i / RPAD; k = i % RPAD; }
       else                             { k = i / R;    m = i % R; }
-      Os[m * LO + k] = v[j];
+      v[j] = (i < R * RPAD && m < rows && k < r)
+                 ? (e.layout == kFactorRowMajor ? e.F[(row0 + m) * r + k]
+                                                : e.F[(int64_t)k * e.ldf + row0 + m])
+                 : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      const int i = b0 + h + j * NH;
+      if (i < R * RPAD) {
+        int m, k;
+        if (e.layout == kFactorRowMajor) { m = i / RPAD; k = i % RPAD; }
+        else                             { k = i / R;    m = i % R; }
+        Os[m * LO + k] = v[j];
+      }
     }
   }
 }
@@ -242,20 +246,21 @@ __device__ void load_old(float* Os, const EpiArgs& e, int R, int64_t row0, int r
 // loaded; rows beyond the slice's valid rows and ranks beyond r are zero).  G rows are staged
 // 32 at a time through Qs from the padded float32 copy; the next 32 are in
 // flight while the current ones are used.
-template <int RPAD>
-__device__ void compute_den(float* Qs, const float* Os, DenTile<RPAD>& den, const float* Gpad,
+template <int RPAD, int NH = kHelpers>
+__device__ void compute_den(float* Qs, const float* Os, DenTile<RPAD, NH>& den, const float* Gpad,
                             int r, int R, int h) {
   constexpr int LQ = ldq<RPAD>();
   constexpr int LO = ldo<RPAD>();
   constexpr int NG = kQsRows * RPAD;
-  constexpr int GV = (NG + kHelpers - 1) / kHelpers;
+  constexpr int GV = (NG + NH - 1) / NH;
   constexpr int KG = RPAD / 8;
-  constexpr int MG = kHelpers / KG;
+  constexpr int MG = NH / KG;
+  constexpr int NA = DenTile<RPAD, NH>::NA;
   const int kg = h % KG, mg = h / KG;
   const bool active = h < KG * MG;
-  auto& acc = den.d;    // up to 8 rows per thread (R <= 64, MG >= 12 for RPAD <= 128)
+  auto& acc = den.d;    // rows mg + (4a + i) MG of the slice
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int a = 0; a < NA; ++a)
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -264,24 +269,24 @@ __device__ void compute_den(float* Qs, const float* Os, DenTile<RPAD>& den, cons
   auto gload = [&](int l0) {
 #pragma unroll
     for (int j = 0; j < GV; ++j) {
-      const int i = h + j * kHelpers;
+      const int i = h + j * NH;
       gv[j] = (i < NG && l0 + i / RPAD < r) ? __ldcg(Gpad + l0 * RPAD + i) : 0.f;
     }
   };
   gload(0);
   for (int l0 = 0; l0 < r; l0 += kQsRows) {
-    helper_sync();   // previous G rows consumed (and Os complete on entry)
+    helper_sync<NH>();   // previous G rows consumed (and Os complete on entry)
 #pragma unroll
     for (int j = 0; j < GV; ++j) {
-      const int i = h + j * kHelpers;
+      const int i = h + j * NH;
       if (i < NG) Qs[(i / RPAD) * LQ + (i % RPAD)] = gv[j];
     }
-    helper_sync();
+    helper_sync<NH>();
     if (l0 + kQsRows < r) gload(l0 + kQsRows);
     const int nl = min(kQsRows, r - l0);
     if (active) {
 #pragma unroll
-      for (int a = 0; a < 2; ++a) {
+      for (int a = 0; a < NA; ++a) {
         if (mg + 4 * a * MG >= R) break;
         int mrow[4];
 #pragma unroll
@@ -309,20 +314,21 @@ __device__ void compute_den(float* Qs, const float* Os, DenTile<RPAD>& den, cons
 // denominators): new values into Ns, and the row-major factor (W) directly.
 // Pass 2 (every thread of the block, rows fastest): the [k][m]-ordered
 // arrays -- the plane(s) and, for H, the factor.
-template <int RPAD, int NT>
-__device__ void finish(float* Ns, const float* Os, const DenTile<RPAD>& den, const EpiArgs& e,
-                       int R, int64_t row0, int rows) {
+template <int RPAD, int NT, int HBASE = kHelperBase, int NH = kHelpers>
+__device__ void finish(float* Ns, const float* Os, const DenTile<RPAD, NH>& den,
+                       const EpiArgs& e, int R, int64_t row0, int rows) {
   constexpr int LN = epi_ldn<RPAD>();
   constexpr int LO = ldo<RPAD>();
-  constexpr int KG = DenTile<RPAD>::KG;
-  constexpr int MG = DenTile<RPAD>::MG;
+  constexpr int KG = DenTile<RPAD, NH>::KG;
+  constexpr int MG = DenTile<RPAD, NH>::MG;
+  constexpr int NA = DenTile<RPAD, NH>::NA;
   const int r = e.r;
   const int tid = threadIdx.x;
-  const int h = tid - kHelperBase;
+  const int h = tid - HBASE;
   if (h >= 0 && h < KG * MG) {
     const int kg = h % KG, mg = h / KG;
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < NA; ++a)
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int m = mg + (4 * a + i) * MG;
