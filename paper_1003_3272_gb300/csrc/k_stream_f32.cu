@@ -63,7 +63,9 @@ struct F32Shape {
   static constexpr int LDA = RPAD + 4;
   static constexpr int ACC = kBM * LDA * 4;
   static constexpr int NSB = tcepi::kRmax * epi_ldn<RPAD>() * 4;
-  static constexpr int DED = tcepi::dedicated_floats<RPAD>() * 4;
+  // helpers' region: staging Qs, old rows Os, denominators Ds
+  static constexpr int DED =
+      (tcepi::dedicated_floats<RPAD>() + tcepi::kRmax * tcepi::ldd<RPAD>()) * 4;
   static constexpr int STAGES_RAW = (kSmemMax - DED - 2048) / STAGE;
   static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
   static constexpr int RING = STAGES * STAGE;
@@ -117,7 +119,7 @@ k_stream_f32(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUt
 
   float* Qs = reinterpret_cast<float*>(smem + Sh::MAIN);
   float* Os = Qs + tcepi::kQsRows * tcepi::ldq<RPAD>();
-  tcepi::DenTile<RPAD, kNH> den;
+  float* Ds = Os + tcepi::kRmax * tcepi::ldo<RPAD>();
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -229,7 +231,6 @@ k_stream_f32(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUt
                             kWaitLimitCycles))
           atomicExch(&s_abort, 1);
       }
-      den.clear();
     } else if (compute) {
       // ---------------- float32 FMA mainloop ----------------
       for (int kb = 0; kb < nkb_run; ++kb) {
@@ -240,20 +241,22 @@ k_stream_f32(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUt
           atomicExch(&s_abort, 1);
           break;
         }
-        const uint8_t* xs = smem + s * Sh::STAGE;
-        const uint8_t* ys = xs + Sh::X_BYTES;
-#pragma unroll 1
+        // 128-byte swizzle: 16-byte chunk c4 of row m sits at chunk c4 ^ (m & 7);
+        // every row this thread reads has the same (m & 7), so one XOR per
+        // chunk places all its loads (immediate row offsets).
+        const uint8_t* xb = smem + s * Sh::STAGE + rg * 128;
+        const uint8_t* yb = smem + s * Sh::STAGE + Sh::X_BYTES + cgi * 128;
+#pragma unroll
         for (int c4 = 0; c4 < 8; ++c4) {
-          // 128-byte swizzle: 16-byte chunk c4 of row m sits at chunk c4 ^ (m & 7)
+          const int xo = (c4 ^ (rg & 7)) << 4;
+          const int yo = (c4 ^ cgi) << 4;
           float4 xv[4], yv[TR];
 #pragma unroll
           for (int i = 0; i < 4; ++i)
-            xv[i] = *reinterpret_cast<const float4*>(xs + (rg + 32 * i) * 128 +
-                                                     ((c4 ^ (rg & 7)) << 4));
+            xv[i] = *reinterpret_cast<const float4*>(xb + i * (32 * 128) + xo);
 #pragma unroll
           for (int t = 0; t < TR; ++t)
-            yv[t] = *reinterpret_cast<const float4*>(ys + (cgi + 8 * t) * 128 +
-                                                     ((c4 ^ cgi) << 4));
+            yv[t] = *reinterpret_cast<const float4*>(yb + t * (8 * 128) + yo);
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -267,12 +270,9 @@ k_stream_f32(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUt
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&empty_bar[s]));
       }
-      den.clear();
     } else if (helper && !*(volatile int*)&s_abort) {
       if (it > 0) tcepi::load_old<RPAD, kNH>(Os, a.ep, R, row0, rows, h);
-      tcepi::compute_den<RPAD, kNH>(Qs, Os, den, a.Gpad, a.r, R, h);
-    } else {
-      den.clear();
+      tcepi::compute_den_smem<RPAD, kNH>(Qs, Os, Ds, a.Gpad, a.r, R, h);
     }
     __syncwarp();
     kb_base += nkb_run;
@@ -306,7 +306,7 @@ k_stream_f32(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUt
     }
     cluster.sync();   // peers are done reading this block's tile
     if (!*(volatile int*)&s_abort)
-      tcepi::finish<RPAD, kThreads, kHelper0, kNH>(Ns, Os, den, a.ep, R, row0, rows);
+      tcepi::finish_smem<RPAD, kThreads>(Ns, Os, Ds, a.ep, R, row0, rows);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
   }

@@ -361,5 +361,114 @@ __device__ void finish(float* Ns, const float* Os, const DenTile<RPAD, NH>& den,
   (void)R;
 }
 
+// Variant for kernels with shared memory to spare: den into Ds[m][k]
+// (stride RPAD + 4), one pass of up to 4 x 8 values per thread at a time
+// (G re-staged per pass), so no denominators live in registers.
+template <int RPAD> __host__ __device__ constexpr int ldd() { return RPAD + 4; }
+
+template <int RPAD, int NH>
+__device__ void compute_den_smem(float* Qs, const float* Os, float* Ds, const float* Gpad,
+                                 int r, int R, int h) {
+  constexpr int LQ = ldq<RPAD>();
+  constexpr int LO = ldo<RPAD>();
+  constexpr int LD = ldd<RPAD>();
+  constexpr int NG = kQsRows * RPAD;
+  constexpr int GV = 16;
+  constexpr int KG = RPAD / 8;
+  constexpr int MG = NH / KG;
+  const int kg = h % KG, mg = h / KG;
+  const bool active = h < KG * MG;
+  for (int mb = mg; mb - mg < R; mb += 4 * MG) {
+    float acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    int mrow[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) mrow[i] = min(mb + i * MG, R - 1);
+    for (int l0 = 0; l0 < r; l0 += kQsRows) {
+      helper_sync<NH>();   // Os complete / previous G rows consumed
+      for (int b = h; b < NG; b += GV * NH) {
+        float gv[GV];
+#pragma unroll
+        for (int j = 0; j < GV; ++j) {
+          const int i = b + j * NH;
+          gv[j] = (i < NG && l0 + i / RPAD < r) ? __ldcg(Gpad + l0 * RPAD + i) : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < GV; ++j) {
+          const int i = b + j * NH;
+          if (i < NG) Qs[(i / RPAD) * LQ + (i % RPAD)] = gv[j];
+        }
+      }
+      helper_sync<NH>();
+      const int nl = min(kQsRows, r - l0);
+      if (active && mb < R) {
+#pragma unroll 2
+        for (int l = 0; l < nl; ++l) {
+          const float4 g0 = *reinterpret_cast<const float4*>(&Qs[l * LQ + kg * 8]);
+          const float4 g1 = *reinterpret_cast<const float4*>(&Qs[l * LQ + kg * 8 + 4]);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float o = Os[mrow[i] * LO + l0 + l];
+            acc[i][0] = fmaf(o, g0.x, acc[i][0]); acc[i][1] = fmaf(o, g0.y, acc[i][1]);
+            acc[i][2] = fmaf(o, g0.z, acc[i][2]); acc[i][3] = fmaf(o, g0.w, acc[i][3]);
+            acc[i][4] = fmaf(o, g1.x, acc[i][4]); acc[i][5] = fmaf(o, g1.y, acc[i][5]);
+            acc[i][6] = fmaf(o, g1.z, acc[i][6]); acc[i][7] = fmaf(o, g1.w, acc[i][7]);
+          }
+        }
+      }
+    }
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int m = mb + i * MG;
+        if (m < R) {
+          *reinterpret_cast<float4*>(&Ds[m * LD + kg * 8]) =
+              make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+          *reinterpret_cast<float4*>(&Ds[m * LD + kg * 8 + 4]) =
+              make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+        }
+      }
+    }
+  }
+}
+
+// finish() with the denominators in Ds: every thread of the block takes part
+// in both passes.
+template <int RPAD, int NT>
+__device__ void finish_smem(float* Ns, const float* Os, const float* Ds, const EpiArgs& e,
+                            int R, int64_t row0, int rows) {
+  constexpr int LN = epi_ldn<RPAD>();
+  constexpr int LO = ldo<RPAD>();
+  constexpr int LD = ldd<RPAD>();
+  const int r = e.r;
+  const int tid = threadIdx.x;
+  if (e.layout == kFactorRowMajor) {
+    for (int i = tid; i < rows * r; i += NT) {
+      const int m = i / r, k = i % r;
+      const float d = __fadd_rn(Ds[m * LD + k], e.eps);
+      const float v = __fdiv_rn(__fmul_rn(Os[m * LO + k], Ns[m * LN + k]), d);
+      e.F[(row0 + m) * r + k] = v;
+      Ns[m * LN + k] = v;
+    }
+    __syncthreads();
+    for (int i = tid; i < rows * r; i += NT) {
+      const int k = i / rows, m = i % rows;
+      store_plane(e, k, row0 + m, Ns[m * LN + k]);
+    }
+  } else {
+    for (int i = tid; i < rows * r; i += NT) {
+      const int k = i / rows, m = i % rows;
+      const float d = __fadd_rn(Ds[m * LD + k], e.eps);
+      const float v = __fdiv_rn(__fmul_rn(Os[m * LO + k], Ns[m * LN + k]), d);
+      e.F[(int64_t)k * e.ldf + row0 + m] = v;
+      store_plane(e, k, row0 + m, v);
+    }
+  }
+  (void)R;
+}
+
 }  // namespace tcepi
 }  // namespace nmf
