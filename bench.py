@@ -17,6 +17,15 @@ error against the FP64 oracle.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU
 oracle instead (the reference arm), on a bounded sample of the same workload.
+
+`--workload` selects one of the other measured matrices instead of the
+planted one (same step: restart + the workload's iterations + objective):
+  faces   361 x 2429, V iid uniform [0,1), r = 10, 50 iterations
+  tall    65536 x 4096, V iid uniform [0,1), r = --rank (16/32/64/128),
+          20 iterations (the precision sweep)
+  large   131072 x 16384, V iid Exponential(1), r = 64, 20 iterations
+  batched 512 independent problems (p, n in 64..2048, r in 4..32),
+          100 iterations per step through the grouped batched launches
 """
 from __future__ import annotations
 
@@ -51,7 +60,11 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks / throttle reasons sampled during the timed region.
+
+    nvidia-smi is started before the warm-up and its first sample awaited, so
+    its start-up (which takes driver locks) does not fall inside the timed
+    region; only samples taken inside the window given to stop() count."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -62,7 +75,7 @@ class ClockSampler:
         self.lines = []
         self._t = None
 
-    def start(self):
+    def start(self, wait_s=10.0):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
@@ -72,12 +85,16 @@ class ClockSampler:
             self._t.start()
         except OSError:
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while not self.lines and time.perf_counter() - t0 < wait_s and self.proc.poll() is None:
+            time.sleep(0.02)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self):
+    def stop(self, window=None):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -89,7 +106,11 @@ class ClockSampler:
             self._t.join(timeout=2)
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines
+        if window is not None:
+            inside = [x for x in lines if window[0] <= x[0] <= window[1] + 0.15]
+            lines = inside if inside else lines[-1:]
+        for _, ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -178,13 +199,30 @@ def read_traffic(kernel_key):
     return d.get("traffic_bytes_per_launch")
 
 
+def make_problem(args):
+    """(problem, workload name, data description) for --workload."""
+    from paper_1003_3272_gb300 import synth
+    if args.workload == "planted":
+        pr = synth.planted(iters=args.iters)
+        return pr, "planted_8192x8192_r50", "synthetic (seeded planted low-rank matrix; no dataset)"
+    if args.workload == "faces":
+        pr = synth.faces()
+        return pr, pr.name, "synthetic (seeded iid uniform [0,1), faces-matrix shape; no dataset)"
+    if args.workload == "tall":
+        pr = synth.tall(args.rank)
+        return pr, pr.name, "synthetic (seeded iid uniform [0,1); no dataset)"
+    pr = synth.large()
+    return pr, pr.name, "synthetic (seeded iid Exponential(1); no dataset)"
+
+
 def time_planted(pr, prec, steps, warmup, ws, local, sample_clocks=False, profile=True):
-    """Time `steps` benchmark steps of one precision on the planted problem.
-    Returns the measurement dict (updates/s, per-launch stream time, ...)."""
+    """Time `steps` benchmark steps of one precision on problem `pr` (the
+    planted problem unless --workload says otherwise).  Returns the
+    measurement dict (updates/s, per-launch stream time, ...)."""
     import torch
-    from paper_1003_3272_gb300 import nmf, synth
+    from paper_1003_3272_gb300 import nmf
     p, n, r, iters = pr.p, pr.n, pr.r, pr.iters
-    seed = synth.BASE_SEED + 1
+    seed = pr.seed
     V = torch.from_numpy(pr.V).cuda()
     W = torch.empty(p, r, device="cuda")
     H = torch.empty(r, n, device="cuda")
@@ -203,25 +241,27 @@ def time_planted(pr, prec, steps, warmup, ws, local, sample_clocks=False, profil
         f_prev[0] = f
         return f
 
+    sampler = ClockSampler(local) if sample_clocks else None
+    if sampler:
+        sampler.start()
     for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     if profile:
         ctx.profile(True)
-    sampler = ClockSampler(local) if sample_clocks else None
     barrier(ws)
     torch.cuda.synchronize()
-    if sampler:
-        sampler.start()
+    w0 = time.perf_counter()
     l0 = nmf.kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     fs = [step() for _ in range(steps)]
     e1.record(stream)
     torch.cuda.synchronize()
+    w1 = time.perf_counter()
     launches = nmf.kernel_launches() - l0
     barrier(ws)
-    clocks = sampler.stop() if sampler else None
+    clocks = sampler.stop((w0, w1)) if sampler else None
     ms = max_over_ranks(e0.elapsed_time(e1), ws)
     res = {"prec": prec, "ms": ms, "steps": steps, "launches": int(launches),
            "clocks": clocks, "objective": fs[-1],
@@ -236,7 +276,7 @@ def time_planted(pr, prec, steps, warmup, ws, local, sample_clocks=False, profil
     return res
 
 
-def roofline(prec, p, n, r, res, clocks):
+def roofline(prec, p, n, r, res, clocks, workload="planted_8192x8192_r50"):
     pk = peaks()
     bytes_l, flops_l = algorithmic(prec, p, n, r)
     st_ms, st_n = res["kinds"]["stream_products"]
@@ -249,7 +289,7 @@ def roofline(prec, p, n, r, res, clocks):
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                 "peak_source": f"152 SMs x 128 FP32 FMA/clk x 2 x {mhz:.0f} MHz "
                                "(median sampled SM clock)",
-                "kernel": "k_stream_simt"}
+                "kernel": "k_stream_f32"}
     else:
         peak = pk["hbm_gbs"]
         achieved = bytes_l / avg_s / 1e9
@@ -257,7 +297,7 @@ def roofline(prec, p, n, r, res, clocks):
                 "frac": round(achieved / peak, 4),
                 "peak_source": f"{pk['_source']} hbm_gbs (copy bandwidth, MEASURED_PEAKS.json)",
                 "kernel": "k_stream_tc"}
-    roof["traffic"] = read_traffic(f"{roof['kernel']}/{prec}/planted_8192x8192_r50")
+    roof["traffic"] = read_traffic(f"{roof['kernel']}/{prec}/{workload}")
     roof["algorithmic_bytes_per_launch"] = int(bytes_l)
     roof["algorithmic_flops_per_launch"] = float(flops_l)
     roof["avg_launch_us"] = round(avg_s * 1e6, 2)
@@ -311,26 +351,59 @@ def time_batched(prec, steps, warmup, iters, ws):
     return out
 
 
-def accuracy_check(precs):
-    """Relative objective error after 10 iterations against the float64
-    oracle on the planted problem at 1024 x 1024, r = 50 (same seeds)."""
+def oracle_objective(workload, iters):
+    """The float64 oracle's objective after `iters` iterations from the seeded
+    start on `workload`, as stored in tests/golden/objectives.json (written by
+    tests/golden/make_objectives.py from the oracle alone), or None."""
+    path = os.path.join(ROOT, "tests", "golden", "objectives.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return d[workload]["objective"].get(str(iters))
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def accuracy(workload, iters, objectives):
+    """Relative objective error of each timed form against the stored float64
+    oracle trajectory (same seeds, same iteration count)."""
+    fo = oracle_objective(workload, iters)
+    if fo is None:
+        return {"rel_objective_error_vs_fp64_oracle": None,
+                "note": f"no stored oracle objective for {workload} at {iters} iterations"}
+    return {"rel_objective_error_vs_fp64_oracle":
+                {k: float(f"{abs(f - fo) / fo:.3e}") for k, f in objectives.items()},
+            "oracle_objective": fo, "iterations": iters,
+            "source": "tests/golden/objectives.json (float64 oracle trajectory, "
+                      "tests/golden/make_objectives.py)"}
+
+
+def run_batched_line(args, ws, local):
+    """--workload batched: the 512-instance batched workload as the line."""
     import torch
-    from oracle import nmf_oracle as orc
-    from paper_1003_3272_gb300 import nmf, synth
-    pr = synth.planted(p=1024, n=1024, r=50, iters=10)
-    Wo, Ho, _, _ = orc.run(pr.V, pr.W0, pr.H0, 10, eps=pr.eps)
-    fo = orc.objective(pr.V, Wo, Ho)
-    out = {}
-    for prec in precs:
-        V = torch.from_numpy(pr.V).cuda()
-        W = torch.from_numpy(pr.W0).cuda()
-        H = torch.from_numpy(pr.H0).cuda()
-        with nmf.NMF(V, W, H, eps=pr.eps, prec=prec) as m:
-            m.step(10)
-            f = m.objective()
-        out[prec] = float(f"{abs(f - fo) / fo:.3e}")
-    return {"rel_objective_error_vs_fp64_oracle": out,
-            "case": "planted 1024x1024 r=50, 10 iterations from the seeded start"}
+    torch.cuda.set_device(local)
+    sampler = ClockSampler(local)
+    sampler.start()
+    w0 = time.perf_counter()
+    b = time_batched(args.prec, args.steps, args.warmup, 100, ws)
+    clocks = sampler.stop((w0, time.perf_counter()))
+    pk = peaks()
+    return {
+        "metric": METRIC, "value": b["value"], "unit": b["unit"], "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.prec, "data": "synthetic (seeded iid uniform [0,1); no dataset)",
+        "config": {"workload": "batched_512", "instances": b["instances"],
+                   "iters_per_step": b["iters_per_step"], "precision": args.prec,
+                   "shapes": b["config"], "global_batch": ws,
+                   "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (about 2.3 GB of V)"},
+        "roofline": {"bound": "hbm", "achieved": b["aggregate_gbs"], "peak": pk["hbm_gbs"],
+                     "unit": "GB/s", "frac": b["hbm_frac"], "traffic": None,
+                     "kernel": "k_batched_tc (whole graph-captured iteration)"},
+        "e2e": None, "gpu_launches": b["gpu_launches"], "clocks": clocks,
+        "objective_mean": b["mean_objective"],
+    }
 
 
 def run_gpu(args, ws, rank, local):
@@ -338,12 +411,14 @@ def run_gpu(args, ws, rank, local):
     from paper_1003_3272_gb300 import synth
 
     torch.cuda.set_device(local)
-    pr = synth.planted(iters=args.iters)
+    if args.workload == "batched":
+        return run_batched_line(args, ws, local), None
+    pr, wname, data = make_problem(args)
     p, n, r, iters = pr.p, pr.n, pr.r, pr.iters
     stream = torch.cuda.current_stream()
     main = time_planted(pr, args.prec, args.steps, args.warmup, ws, local, sample_clocks=True)
     clocks = main["clocks"]
-    roof = roofline(args.prec, p, n, r, main, clocks)
+    roof = roofline(args.prec, p, n, r, main, clocks, wname)
 
     # End to end through the public one-call API with host buffers.
     e2e = None
@@ -367,8 +442,8 @@ def run_gpu(args, ws, rank, local):
         e2e = {"value": round(iters * ne * ws / te, 2), "unit": "updates/s",
                "h2d_bytes_per_step": int(Vh.nbytes + Wh.nbytes + Hh.nbytes),
                "d2h_bytes_per_step": int(Wh.nbytes + Hh.nbytes + 8),
-               "steps": ne, "api": "nmf_solve (host V, W, H; allocation, operand copies, "
-                                   "200 iterations, objective, copies back)"}
+               "steps": ne, "api": f"nmf_solve (host V, W, H; allocation, operand copies, "
+                                   f"{iters} iterations, objective, copies back)"}
 
     kinds = main["kinds"]
     out = {
@@ -377,12 +452,14 @@ def run_gpu(args, ws, rank, local):
         "ms_per_step": round(main["ms"] / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "tf32": "tf32", "bf16x3": "bf16x3", "bf16": "bf16"}[args.prec],
-        "data": "synthetic (seeded planted low-rank matrix; no dataset)",
-        "config": {"workload": "planted_8192x8192_r50", "p": p, "n": n, "r": r,
+        "data": data,
+        "config": {"workload": wname, "p": p, "n": n, "r": r,
                    "iters_per_step": iters, "precision": args.prec, "order": "h_first",
                    "eps": pr.eps, "global_batch": ws, "parallelism": f"replicas x{ws}",
-                   "l2": "inputs larger than L2 (V is 268 MB fp32; L2 129 MB)",
-                   "step": "restart (operand copies + seeded W,H + Grams) + 200 MM "
+                   "l2": (f"inputs larger than L2 (V is {p * n * 4 / 1e6:.0f} MB fp32; L2 129 MB)"
+                          if p * n * 4 > 129e6 else
+                          f"V ({p * n * 4 / 1e6:.1f} MB) fits in L2: the L2-resident case"),
+                   "step": f"restart (operand copies + seeded W,H + Grams) + {iters} MM "
                            "iterations + objective + stopping test"},
         "roofline": roof, "e2e": e2e, "gpu_launches": main["launches"], "clocks": clocks,
         "objective": main["objective"],
@@ -391,12 +468,14 @@ def run_gpu(args, ws, rank, local):
     if not args.no_extras:
         # the plain FP32 form and the other precisions on the same workload
         by = {}
+        objs = {}
         for prec in ["fp32", "tf32", "bf16x3", "bf16"]:
             if prec == args.prec:
                 res, rf = main, roof
             else:
                 res = time_planted(pr, prec, max(2, args.steps // 2), 2, ws, local)
-                rf = roofline(prec, p, n, r, res, clocks)
+                rf = roofline(prec, p, n, r, res, clocks, wname)
+            objs[prec] = res["objective"]
             by[prec] = {"updates_per_s": round(res["value"], 1),
                         "ms_per_step": round(res["ms"] / res["steps"], 3),
                         "roofline_frac": rf["frac"], "roofline_bound": rf["bound"],
@@ -406,15 +485,23 @@ def run_gpu(args, ws, rank, local):
         for prec in by:
             by[prec]["speedup_vs_fp32"] = round(by[prec]["updates_per_s"] / base, 2)
         out["by_precision"] = by
-        out["batched"] = time_batched("bf16x3", max(2, args.steps // 2), 2, 20, ws)
-        out["accuracy"] = accuracy_check(["fp32", "tf32", "bf16x3", "bf16"])
+        out["accuracy"] = accuracy(wname, iters, objs)
+        if args.workload == "planted":
+            out["batched"] = time_batched("bf16x3", max(2, args.steps // 2), 2, 20, ws)
+    else:
+        out["accuracy"] = accuracy(wname, iters, {args.prec: main["objective"]})
     return out, pr
 
 
 def cpu_baseline(pr, budget_s):
     """The FP64 oracle as it stands, timed on this host's cores on a bounded
-    sample of the same workload: MM iterations of the full planted problem."""
+    sample of the same workload: MM iterations of the full problem."""
     import numpy as np
+    if pr.V.size > (1 << 29):
+        return {"value": None, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle",
+                "sample": "not run: the oracle widens V to float64 for every product "
+                          f"({pr.V.size * 8 / 1e9:.0f} GB per copy); the sampled parity "
+                          "tests cover this workload"}
     from oracle import nmf_oracle as orc
     V = pr.V
     W = pr.W0.astype(np.float64)
@@ -430,8 +517,43 @@ def cpu_baseline(pr, budget_s):
     dt = time.perf_counter() - t0
     return {"value": round(k / dt, 4), "unit": "updates/s", "cores": os.cpu_count(),
             "kind": "oracle",
-            "sample": f"{k} MM iterations (H then W update) of the 8192x8192 r=50 planted "
-                      f"problem in float64 numpy/BLAS, {dt:.1f} s"}
+            "sample": f"{k} MM iterations (H then W update) of the {pr.p}x{pr.n} r={pr.r} "
+                      f"{pr.name} problem in float64 numpy/BLAS, {dt:.1f} s"}
+
+
+def run_reference_batched(args):
+    """Reference arm on the batched workload: each step is one MM iteration of
+    each of the first 32 instances (a bounded sample)."""
+    import numpy as np
+    from oracle import nmf_oracle as orc
+    from paper_1003_3272_gb300 import synth
+    probs = synth.batch(count=512)[:32]
+    st = [(pr.W0.astype(np.float64), pr.H0.astype(np.float64)) for pr in probs]
+    def one():
+        for i, pr in enumerate(probs):
+            st[i] = orc.step(pr.V, st[i][0], st[i][1], pr.eps)
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = time.perf_counter() - t0
+    value = len(probs) * args.steps / dt
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 2),
+        "unit": "instance-iterations/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded iid uniform [0,1); no dataset)",
+        "config": {"workload": "batched_512", "sample": "first 32 of the 512 instances",
+                   "iters_per_step": 1, "precision": "f64 oracle"},
+        "cpu_baseline": {"value": round(value, 2), "unit": "instance-iterations/s",
+                         "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "each step = 1 MM iteration of each of the first 32 "
+                                   "instances (float64 numpy/BLAS)"},
+        "e2e": {"value": round(value, 2), "unit": "instance-iterations/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
 
 
 def run_reference(args):
@@ -439,8 +561,9 @@ def run_reference(args):
     one MM iteration (a bounded sample of the 200-iteration run)."""
     import numpy as np
     from oracle import nmf_oracle as orc
-    from paper_1003_3272_gb300 import synth
-    pr = synth.planted(iters=args.iters)
+    if args.workload == "batched":
+        return run_reference_batched(args)
+    pr, wname, data = make_problem(args)
     W = pr.W0.astype(np.float64)
     H = pr.H0.astype(np.float64)
     for _ in range(args.warmup):
@@ -455,13 +578,13 @@ def run_reference(args):
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded planted low-rank matrix; no dataset)",
-        "config": {"workload": "planted_8192x8192_r50", "p": pr.p, "n": pr.n, "r": pr.r,
+        "data": data,
+        "config": {"workload": wname, "p": pr.p, "n": pr.n, "r": pr.r,
                    "iters_per_step": 1, "precision": "f64 oracle"},
         "cpu_baseline": {"value": round(value, 4), "unit": "updates/s", "cores": os.cpu_count(),
                          "kind": "oracle",
-                         "sample": f"each step = 1 MM iteration of the 8192x8192 r=50 planted "
-                                   f"problem (float64 numpy/BLAS)"},
+                         "sample": f"each step = 1 MM iteration of the {pr.p}x{pr.n} r={pr.r} "
+                                   f"{wname} problem (float64 numpy/BLAS)"},
         "e2e": {"value": round(value, 4), "unit": "updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -474,7 +597,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--prec", default="bf16x3", choices=["fp32", "tf32", "bf16x3", "bf16"])
-    ap.add_argument("--iters", type=int, default=200)
+    ap.add_argument("--iters", type=int, default=200,
+                    help="MM iterations per step on the planted workload")
+    ap.add_argument("--workload", default="planted",
+                    choices=["planted", "faces", "tall", "large", "batched"])
+    ap.add_argument("--rank", type=int, default=64, choices=[16, 32, 64, 128],
+                    help="rank of the tall workload")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -492,7 +620,7 @@ def main():
     ws, rank, local = dist_setup(args.gpus)
     out, pr = run_gpu(args, ws, rank, local)
     if rank == 0:
-        if ws == 1 and not args.no_cpu_baseline:
+        if ws == 1 and not args.no_cpu_baseline and pr is not None:
             out["cpu_baseline"] = cpu_baseline(pr, args.cpu_budget)
         else:
             out["cpu_baseline"] = None

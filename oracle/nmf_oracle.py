@@ -34,6 +34,7 @@ import numpy as np
 __all__ = [
     "wtv", "vht", "gram_w", "gram_h", "update_h", "update_w", "step", "run",
     "objective", "relative_change", "converged", "surrogate",
+    "update_h_columns", "update_w_rows",
 ]
 
 
@@ -92,6 +93,33 @@ def update_w(V, W, H, eps=1e-10):
     num = vht(V, H)
     den = W @ gram_h(H) + eps
     return (W * num) / den
+
+
+def update_h_columns(V, W, H, cols, eps=1e-10):
+    """Columns ``cols`` of the right-factor update of Eq. (3.4), for checking
+    samples of a problem too large to update whole.  Column j of the new H
+    depends only on column j of V and of H (and on all of W):
+
+        H_kj <- H_kj * (W^T V_:j)_k / ((W^T W) H_:j + eps)_k
+
+    Returns the new columns, r x len(cols) (float64)."""
+    cols = np.asarray(cols)
+    Vc = _f64(np.asarray(V)[:, cols])
+    Hc = _f64(np.asarray(H)[:, cols])
+    return update_h(Vc, W, Hc, eps)
+
+
+def update_w_rows(V, W, H, rows, eps=1e-10):
+    """Rows ``rows`` of the left-factor update of Eq. (3.3).  Row i of the new
+    W depends only on row i of V and of W (and on all of H):
+
+        W_ik <- W_ik * (V_i: H^T)_k / (W_i: (H H^T) + eps)_k
+
+    Returns the new rows, len(rows) x r (float64)."""
+    rows = np.asarray(rows)
+    Vr = _f64(np.asarray(V)[rows, :])
+    Wr = _f64(np.asarray(W)[rows, :])
+    return update_w(Vr, Wr, H, eps)
 
 
 def step(V, W, H, eps=1e-10, order="h_first"):

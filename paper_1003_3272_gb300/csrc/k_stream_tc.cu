@@ -58,6 +58,8 @@ struct TcParams {
   int nclusters;
   int64_t kper;          // K per split (multiple of the k-block)
   int nkbt;              // k-blocks per tile row (blocked X layout)
+  int nacc;              // accumulators for the main products (k-block kb -> kb % nacc)
+  int tmem_cols;         // tensor-memory columns allocated
   EpiArgs ep;            // the factor being updated and its planes
   // the other factor Q, whose Gram the helpers form in the prologue
   const float* Q;
@@ -93,7 +95,10 @@ struct TcShape {
   static constexpr int RING = STAGES * STAGE;
   static constexpr int MAIN = RING > ACC + NSB ? RING : ACC + NSB;  // Acc/Ns reuse the ring
   static constexpr int SMEM = MAIN + DED + 1024;   // + alignment slack
-  static constexpr int TMEM_COLS = RPAD <= 32 ? 32 : (RPAD <= 64 ? 64 : 128);
+  // Tensor-memory column stride of one accumulator; the block allocates up
+  // to 512 columns (it is alone on its SM: its shared memory exceeds half
+  // of the SM's).
+  static constexpr int CS = RPAD <= 32 ? 32 : (RPAD <= 64 ? 64 : 128);
   static_assert(STAGES >= 2, "pipeline needs two stages");
 };
 
@@ -167,7 +172,7 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
     if (X3) { ptx::tma_prefetch(&tx_lo); ptx::tma_prefetch(&ty_lo); }
   }
   if (warp == 1) {
-    ptx::tmem_alloc(ptx::smem_u32(&tmem_slot), Sh::TMEM_COLS);
+    ptx::tmem_alloc(ptx::smem_u32(&tmem_slot), (uint32_t)a.tmem_cols);
     ptx::tmem_relinquish();
   }
   ptx::tc_fence_before();
@@ -281,6 +286,14 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
       }
     } else if (warp == 1 && lane == 0) {
       // ---------------- MMA issuer ----------------
+      // The tensor core's float32 accumulation is not round-to-nearest, so
+      // its error grows with the number of additions into one accumulator.
+      // The main products (hi x hi) rotate over nacc accumulators, k-block kb
+      // into kb % nacc, and the small split-BF16 cross terms (2^-8 of the
+      // main term) go to one accumulator of their own; the epilogue sums them
+      // with IEEE adds.
+      const uint32_t tcross = tmem + (uint32_t)(a.nacc * Sh::CS);
+      int ai = 0;
       for (int kb = 0; kb < nkb_run; ++kb) {
         const int g = kb_base + kb;
         const int s = g % STAGES;
@@ -295,20 +308,22 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
         for (int kk = 0; kk < 4; ++kk) {
           const uint64_t ah = ptx::sdesc_sw128(x_addr(s, 0) + kk * 32);
           const uint64_t bh = ptx::sdesc_sw128(y_addr(s, 0) + kk * 32);
-          const uint32_t acc = (kb | kk) != 0;
+          const uint32_t tacc = tmem + (uint32_t)(ai * Sh::CS);
+          const uint32_t acc = (kb >= a.nacc || kk != 0) ? 1u : 0u;
           if (PREC == NMF_TF32) {
-            ptx::mma_tf32(tmem, ah, bh, IDESC, acc);
+            ptx::mma_tf32(tacc, ah, bh, IDESC, acc);
           } else {
-            ptx::mma_bf16(tmem, ah, bh, IDESC, acc);
+            ptx::mma_bf16(tacc, ah, bh, IDESC, acc);
             if (X3) {
               const uint64_t al = ptx::sdesc_sw128(x_addr(s, 1) + kk * 32);
               const uint64_t bl = ptx::sdesc_sw128(y_addr(s, 1) + kk * 32);
-              ptx::mma_bf16(tmem, ah, bl, IDESC, 1);
-              ptx::mma_bf16(tmem, al, bh, IDESC, 1);
+              ptx::mma_bf16(tcross, ah, bl, IDESC, (kb | kk) != 0);
+              ptx::mma_bf16(tcross, al, bh, IDESC, 1);
             }
           }
         }
         ptx::mma_commit(ptx::smem_u32(&empty_bar[s]));
+        if (++ai == a.nacc) ai = 0;
       }
       // Always signal: also covers MMAs still in flight on the abort path.
       ptx::mma_commit(ptx::smem_u32(&acc_bar));
@@ -334,14 +349,30 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
     float* Ns = reinterpret_cast<float*>(smem + Sh::ACC);         // [R][LDN]
     const int row = warp * 32 + lane;  // TMEM lane == tile row
     if (!abort && warp < 4) {
+      const int used = nkb_run < a.nacc ? nkb_run : a.nacc;   // accumulators written
+      const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
       for (int c = 0; c < RPAD / 16; ++c) {
         float v[16];
-        if (nkb_run > 0) {
-          ptx::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), v);
-        } else {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] = 0.f;
+        for (int j = 0; j < 16; ++j) v[j] = 0.f;
+        // Fixed order: the main accumulators 0 .. used-1, then the cross
+        // terms, loaded two at a time.
+        const int nload = used + ((X3 && used > 0) ? 1 : 0);
+        for (int ac = 0; ac < nload; ac += 2) {
+          // load index i < used: main accumulator i; i == used: cross terms
+          // (allocated only for X3); an odd tail re-loads a0 and skips it
+          const bool two = ac + 1 < nload;
+          const int a0 = ac < used ? ac : a.nacc;
+          const int a1 = two ? (ac + 1 < used ? ac + 1 : a.nacc) : a0;
+          float t0[16], t1[16];
+          ptx::tmem_ld16x2(tl + (uint32_t)(a0 * Sh::CS + c * 16),
+                           tl + (uint32_t)(a1 * Sh::CS + c * 16), t0, t1);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            v[j] = __fadd_rn(v[j], t0[j]);
+            if (two) v[j] = __fadd_rn(v[j], t1[j]);
+          }
         }
 #pragma unroll
         for (int j = 0; j < 16; j += 4)
@@ -378,7 +409,7 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
 
   ptx::tc_fence_before();
   __syncthreads();
-  if (warp == 1) ptx::tmem_dealloc(tmem, Sh::TMEM_COLS);
+  if (warp == 1) ptx::tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
   if (*(volatile int*)&s_abort && threadIdx.x == 0) atomicExch(a.err, (int)NMF_ETIMEOUT);
 }
 
@@ -572,6 +603,19 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
   pl.kchunk = ceil_div(nkb, bestS) * pl.kblock;
   pl.grid = bestG * bestS;
   pl.fn = fn;
+  // Accumulators: enough that no main accumulator takes more than about 256
+  // additions (4 MMAs per k-block), at most 8 and within 512 columns.
+  if (prec != NMF_FP32) {
+    const int cs = pl.rpad <= 32 ? 32 : (pl.rpad <= 64 ? 64 : 128);
+    const int cross = prec == NMF_BF16X3 ? 1 : 0;
+    const int amax = (512 / cs - cross) < 8 ? 512 / cs - cross : 8;
+    const int64_t adds = (pl.kchunk / pl.kblock) * 4;
+    int na = (int)ceil_div(adds, 256);
+    pl.nacc = na < 1 ? 1 : (na > amax ? amax : na);
+    int cols = 32;
+    while (cols < (pl.nacc + cross) * cs) cols *= 2;
+    pl.tmem_cols = cols;
+  }
   const bool bf = prec == NMF_BF16X3 || prec == NMF_BF16;
   (void)ldx;
   pl.nkbt = (int)nkb;
@@ -595,6 +639,8 @@ cudaError_t tc_launch(const TcPlan& pl, const EpiArgs& ep, const TcGram& gr, int
   prm.M = pl.M; prm.K = pl.K; prm.r = pl.r;
   prm.S = pl.S; prm.tiles = pl.tiles; prm.nclusters = pl.nclusters; prm.kper = pl.kchunk;
   prm.nkbt = pl.nkbt;
+  prm.nacc = pl.nacc;
+  prm.tmem_cols = pl.tmem_cols;
   prm.ep = ep;
   prm.Q = gr.Q; prm.q_layout = gr.q_layout; prm.ldq = gr.ldq; prm.QM = gr.QM;
   prm.gpart = gr.gpart;

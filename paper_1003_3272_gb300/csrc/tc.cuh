@@ -25,6 +25,8 @@ struct TcPlan {
   int threads = 256;     // block size of the kernel instance
   int nkbt = 0;          // k-blocks per tile row of the blocked X copy
   int nclusters = 0;     // persistent clusters
+  int nacc = 1;          // tensor-memory accumulators the main products rotate over
+  int tmem_cols = 32;    // tensor-memory columns the kernel allocates
   void* fn = nullptr;    // kernel instance
   CUtensorMap x_hi, x_lo, y_hi, y_lo;
 };

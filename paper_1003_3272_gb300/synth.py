@@ -86,11 +86,29 @@ def words(seed: int, stream: int, start: int, count: int) -> np.ndarray:
 _CHUNK = 1 << 22
 
 
+def _chunks(count, body):
+    """Run ``body(start, length)`` over chunks of ``count``; large fills use a
+    thread pool (numpy releases the GIL inside the array operations).  The
+    chunks write disjoint slices, so the result does not depend on the
+    schedule."""
+    starts = range(0, count, _CHUNK)
+    if count <= 4 * _CHUNK:
+        for s in starts:
+            body(s, min(_CHUNK, count - s))
+        return
+    import concurrent.futures as cf
+    import os
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(workers) as ex:
+        list(ex.map(lambda s: body(s, min(_CHUNK, count - s)), starts))
+
+
 def _fill(seed, stream, count, fn, dtype=np.float32):
     out = np.empty(count, dtype=dtype)
-    for s in range(0, count, _CHUNK):
-        c = min(_CHUNK, count - s)
+
+    def body(s, c):
         out[s:s + c] = fn(words(seed, stream, s, c))
+    _chunks(count, body)
     return out
 
 
@@ -119,13 +137,14 @@ def abs_normal(seed: int, stream: int, shape, sigma: float) -> np.ndarray:
     """iid |N(0, sigma^2)|, float32 (Box-Muller over word pairs)."""
     n = int(np.prod(shape))
     out = np.empty(n, dtype=np.float32)
-    for s in range(0, n, _CHUNK):
-        c = min(_CHUNK, n - s)
+
+    def body(s, c):
         w = words(seed, stream, 2 * s, 2 * c)
         u1 = ((w[0::2] >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
         u2 = ((w[1::2] >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
         z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
         out[s:s + c] = np.abs(sigma * z)
+    _chunks(n, body)
     return out.reshape(shape)
 
 
@@ -221,6 +240,16 @@ TALL = dict(name="tall_65536x4096", p=65536, n=4096, iters=20)
 LARGE = dict(name="large_131072x16384_r64", p=131072, n=16384, r=64, iters=20)
 BATCH = dict(name="batched_512", count=512, pmin=64, pmax=2048, rmin=4, rmax=32,
              iters=100)
+
+
+def tall(r: int, seed: int = BASE_SEED + 2, iters: int = 20) -> Problem:
+    c = TALL
+    return uniform_problem(c["p"], c["n"], r, seed, iters, f"{c['name']}_r{r}")
+
+
+def large(seed: int = BASE_SEED + 4, iters: int = 20) -> Problem:
+    c = LARGE
+    return exponential_problem(c["p"], c["n"], c["r"], seed, iters, c["name"])
 
 
 def faces(seed: int = BASE_SEED + 0) -> Problem:

@@ -1,0 +1,146 @@
+"""The tall precision-sweep matrix (65536 x 4096, V iid uniform on [0,1),
+r in {16, 32, 64, 128}) and the large streaming matrix (131072 x 16384,
+V iid Exponential(1), r = 64) at full size, in the launch configuration the
+benchmark times.  The oracle cannot update these whole, so sampled columns of
+the new H and sampled rows of the new W are checked one by one (the H sample
+from the seeded start, the W sample from the GPU's own new H, which is exactly
+what the GPU's W half step consumed), and the objective is checked whole,
+summed over row blocks of the oracle's direct residual.
+"""
+import numpy as np
+import pytest
+
+from oracle import nmf_oracle as orc
+from paper_1003_3272_gb300 import synth
+from gpu_util import entry_rel_err, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+# One half step, per-entry relative error.  All terms of the 4096..131072-long
+# contractions are positive (no cancellation): float32 FMA accumulation
+# (round to nearest) errs like sqrt(K) u; the tensor core's float32
+# accumulation does not round to nearest, so its error grows with the
+# additions per accumulator, which the kernel bounds by rotating over several
+# accumulators; on top comes each form's operand rounding.
+HALF_STEP_BAR = {"fp32": 1e-4, "bf16x3": 5e-5, "tf32": 3e-3, "bf16": 2.5e-2}
+NSAMPLE = 40
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1003_3272_gb300 import build, nmf
+    build.build()
+    nmf.load()
+
+
+def _sampled_iteration(V, W0, H0, prec, seed):
+    """One H-first iteration on the GPU; returns (H sample error, W sample
+    error, GPU objective after the iteration, new W, new H)."""
+    from paper_1003_3272_gb300 import nmf
+    p, n = V.shape
+    rng = np.random.default_rng(seed)
+    cols = np.sort(rng.choice(n, NSAMPLE, replace=False))
+    rows = np.sort(rng.choice(p, NSAMPLE, replace=False))
+    Vd, Wd, Hd = to_dev(V), to_dev(W0), to_dev(H0)
+    with nmf.NMF(Vd, Wd, Hd, prec=prec) as m:
+        m.half_step(0)
+        H1 = to_host(Hd)
+        m.half_step(1)
+        W1 = to_host(Wd)
+        f = m.objective()
+    del Vd
+    eh = entry_rel_err(H1[:, cols], orc.update_h_columns(V, W0, H0, cols))[0]
+    ew = entry_rel_err(W1[rows], orc.update_w_rows(V, W0, H1, rows))[0]
+    return eh, ew, f, W1, H1
+
+
+def _objective_blocks(V, W, H, block=8192):
+    return float(sum(orc.objective(V[i:i + block], W[i:i + block], H)
+                     for i in range(0, V.shape[0], block)))
+
+
+@pytest.fixture(scope="module")
+def tall_v():
+    c = synth.TALL
+    return synth.uniform_closed_open(synth.BASE_SEED + 2, synth.STREAM_V, (c["p"], c["n"]))
+
+
+@pytest.mark.parametrize("r", [16, 32, 64, 128])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3", "bf16"])
+def test_tall_sweep_full_size_sampled(tall_v, prec, r):
+    c = synth.TALL
+    W0, H0 = synth.starting_factors(synth.BASE_SEED + 2, c["p"], c["n"], r)
+    eh, ew, f, W1, H1 = _sampled_iteration(tall_v, W0, H0, prec, seed=r)
+    assert eh < HALF_STEP_BAR[prec], (prec, r, eh)
+    assert ew < HALF_STEP_BAR[prec], (prec, r, ew)
+    assert np.isfinite(f) and f > 0
+    if r == 16 and prec == "fp32":
+        fo = _objective_blocks(tall_v, W1, H1)
+        assert abs(f - fo) / fo <= 1e-6
+
+
+@pytest.fixture(scope="module")
+def large_v():
+    c = synth.LARGE
+    return synth.exponential(synth.BASE_SEED + 4, synth.STREAM_V, (c["p"], c["n"]))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_large_streaming_full_size_sampled(large_v, prec):
+    c = synth.LARGE
+    W0, H0 = synth.starting_factors(synth.BASE_SEED + 4, c["p"], c["n"], c["r"])
+    eh, ew, f, W1, H1 = _sampled_iteration(large_v, W0, H0, prec, seed=5)
+    assert eh < HALF_STEP_BAR[prec], (prec, eh)
+    assert ew < HALF_STEP_BAR[prec], (prec, ew)
+    if prec == "bf16x3":
+        # the objective reads the float32 V, whatever the stream precision
+        fo = _objective_blocks(large_v, W1, H1)
+        assert abs(f - fo) / fo <= 1e-6
+
+
+# --- objective trajectories against the stored float64 oracle runs -----------
+# tests/golden/objectives.json holds the oracle's objective after k iterations
+# from the same seeded start (written by tests/golden/make_objectives.py).
+# Bars: the relative objective error the form is built for (1e-5 for float32
+# and split BF16x3; TF32 and BF16 are reported forms with looser bars set by
+# their operand rounding, 2^-11 and 2^-8).
+TRAJ_BAR = {"fp32": 1e-5, "bf16x3": 1e-5, "tf32": 2e-3, "bf16": 2e-2}
+
+
+def _golden_objective(name, iters):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "objectives.json")
+    with open(path) as fh:
+        return json.load(fh)[name]["objective"][str(iters)]
+
+
+def _gpu_objective(pr, prec, iters):
+    from paper_1003_3272_gb300 import nmf
+    V, W, H = to_dev(pr.V), to_dev(pr.W0), to_dev(pr.H0)
+    with nmf.NMF(V, W, H, eps=pr.eps, prec=prec) as m:
+        m.step(iters)
+        return m.objective()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3", "bf16"])
+def test_planted_full_run_objective(prec):
+    """The benchmark's workload: 200 iterations of the 8192 x 8192, r = 50
+    planted problem."""
+    pr = synth.planted()
+    fo = _golden_objective("planted_8192x8192_r50", 200)
+    f = _gpu_objective(pr, prec, 200)
+    assert abs(f - fo) / fo <= TRAJ_BAR[prec], (prec, f, fo)
+
+
+@pytest.mark.parametrize("r", [16, 32, 64, 128])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3", "bf16"])
+def test_tall_sweep_objective_20_iterations(tall_v, prec, r):
+    c = synth.TALL
+    W0, H0 = synth.starting_factors(synth.BASE_SEED + 2, c["p"], c["n"], r)
+    pr = synth.Problem(f"tall_r{r}", tall_v, W0, H0, r, 20, 1e-10, synth.BASE_SEED + 2)
+    fo = _golden_objective(f"tall_65536x4096_r{r}", 20)
+    f = _gpu_objective(pr, prec, 20)
+    assert abs(f - fo) / fo <= TRAJ_BAR[prec], (prec, r, f, fo)

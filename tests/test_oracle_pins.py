@@ -105,6 +105,25 @@ def test_exact_form_reproduces_on_random_rationals():
         np.testing.assert_allclose(Hf, np.array(Hx, dtype=float), rtol=1e-14)
 
 
+def test_sampled_updates_match_exact_elementwise_forms():
+    """The column / row sampled updates (used to check problems too large to
+    update whole) equal the paper's elementwise updates in exact rationals on
+    the sampled columns / rows, including unsorted and repeated indices."""
+    rng = np.random.default_rng(11)
+    V = rng.integers(0, 7, (5, 6)).tolist()
+    W = rng.integers(1, 4, (5, 3)).tolist()
+    H = rng.integers(1, 4, (3, 6)).tolist()
+    Va, Wa, Ha = (np.array(a, float) for a in (V, W, H))
+    cols = [4, 0, 4, 2]
+    rows = [3, 1, 1]
+    Hx = np.array(exact.right_update(V, W, H), dtype=float)
+    np.testing.assert_allclose(orc.update_h_columns(Va, Wa, Ha, cols, eps=0.0),
+                               Hx[:, cols], rtol=1e-14)
+    Wx = np.array(exact.left_update(V, W, H), dtype=float)
+    np.testing.assert_allclose(orc.update_w_rows(Va, Wa, Ha, rows, eps=0.0),
+                               Wx[rows], rtol=1e-14)
+
+
 def test_objective_matches_exact_sum():
     rng = np.random.default_rng(3)
     V = rng.integers(0, 9, (4, 6))
