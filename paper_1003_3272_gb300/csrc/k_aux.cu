@@ -31,97 +31,95 @@ __global__ void k_seed_uniform(float* dst, int64_t count, uint64_t key) {
 // ---------------------------------------------------------------------------
 // Operand copies of V.
 // ---------------------------------------------------------------------------
-__global__ void k_copy_pad(const float* __restrict__ src, int64_t rows, int64_t cols,
-                           int64_t lds, float* __restrict__ dst, int64_t ldd, int tf32) {
-  const int64_t total = rows * ldd;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / ldd, c = i % ldd;
-    const float v = c < cols ? src[r * lds + c] : 0.f;
-    dst[i] = tf32 ? round_tf32(v) : v;
-  }
-}
-
-// dst (cols x ldd) = src (rows x cols)^T, zero in columns rows..ldd-1.
-__global__ void k_transpose_pad(const float* __restrict__ src, int64_t rows, int64_t cols,
-                                int64_t lds, float* __restrict__ dst, int64_t ldd, int tf32) {
-  __shared__ float t[32][33];
-  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
-  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-    const int64_t r = r0 + y, c = c0 + threadIdx.x;
-    t[y][threadIdx.x] = (r < rows && c < cols) ? src[r * lds + c] : 0.f;
-  }
-  __syncthreads();
-  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-    const int64_t c = c0 + y, r = r0 + threadIdx.x;  // dst row c, column r
-    if (c < cols && r < ldd) {
-      const float v = t[threadIdx.x][y];
-      dst[c * ldd + r] = tf32 ? round_tf32(v) : v;
-    }
-  }
-}
-
-// hi = bf16(v), lo = bf16(v - hi); optional transpose; zero padding.
-__global__ void k_split_bf16(const float* __restrict__ src, int64_t rows, int64_t cols,
-                             int64_t lds, int transpose, __nv_bfloat16* __restrict__ hi,
-                             __nv_bfloat16* __restrict__ lo, int64_t ldd) {
-  __shared__ float t[32][33];
-  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
-  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-    const int64_t r = r0 + y, c = c0 + threadIdx.x;
-    t[y][threadIdx.x] = (r < rows && c < cols) ? src[r * lds + c] : 0.f;
-  }
-  __syncthreads();
-  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-    int64_t orow, ocol;
-    float v;
-    if (transpose) { orow = c0 + y; ocol = r0 + threadIdx.x; v = t[threadIdx.x][y];
-                     if (orow >= cols) continue; }
-    else           { orow = r0 + y; ocol = c0 + threadIdx.x; v = t[y][threadIdx.x];
-                     if (orow >= rows) continue; }
-    if (ocol >= ldd) continue;
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    hi[orow * ldd + ocol] = h;
-    if (lo) lo[orow * ldd + ocol] = __float2bfloat16_rn(__fsub_rn(v, __bfloat162float(h)));
-  }
-}
-
 // Tile-blocked operand copy of V for the tensor-core products.  The output
 // is the M x K matrix (V itself, or V^T when `transpose`) cut into blocks of
 // 128 rows x KBE columns (KBE = 64 bf16 or 32 tf32 = 128 bytes); block
 // (mt, kb) is stored contiguously (row pitch 128 bytes) at block index
 // mt * nkb + kb, so one tile's K range is a single contiguous stream.
 // mode 0: bf16 hi (and lo = bf16(v - hi) when lo != null); mode 1: tf32;
-// mode 2: float32 as is.
-// Entries outside M x K are never written (the buffer starts zeroed).
-__global__ void k_operand_blocked(const float* __restrict__ src, int64_t rows, int64_t cols,
-                                  int64_t lds, int transpose, int mode, void* __restrict__ hi,
-                                  void* __restrict__ lo, int64_t nkb, int kbe) {
-  __shared__ float t[32][33];
-  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
-  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-    const int64_t r = r0 + y, c = c0 + threadIdx.x;
-    t[y][threadIdx.x] = (r < rows && c < cols) ? src[r * lds + c] : 0.f;
+// mode 2: float32 as is.  Entries of a block outside M x K are written as 0.
+//
+// One CTA writes one output block: 16-byte loads of V (coalesced rows), and
+// 4 consecutive K values per thread stored as one 8-byte (bf16) or 16-byte
+// (float32) store, so each warp writes 256 or 512 contiguous bytes.  The
+// transposed copy goes through a [KBE][128] shared-memory tile.
+constexpr int kObThreads = 256;
+constexpr int kObLd = 129;
+
+__device__ __forceinline__ float4 load4(const float* s, int64_t idx, int64_t lim, bool vec) {
+  // V[idx .. idx+3] with entries at or past `lim` (the row's end) read as 0
+  if (vec && idx + 3 < lim) return __ldcs(reinterpret_cast<const float4*>(s + idx));
+  float4 v;
+  v.x = idx < lim ? __ldcs(s + idx) : 0.f;
+  v.y = idx + 1 < lim ? __ldcs(s + idx + 1) : 0.f;
+  v.z = idx + 2 < lim ? __ldcs(s + idx + 2) : 0.f;
+  v.w = idx + 3 < lim ? __ldcs(s + idx + 3) : 0.f;
+  return v;
+}
+
+__device__ __forceinline__ void store4(void* hi, void* lo, int64_t off, int mode, float4 v) {
+  if (mode == 2) {
+    *reinterpret_cast<float4*>(static_cast<float*>(hi) + off) = v;
+  } else if (mode == 1) {
+    *reinterpret_cast<float4*>(static_cast<float*>(hi) + off) =
+        make_float4(round_tf32(v.x), round_tf32(v.y), round_tf32(v.z), round_tf32(v.w));
+  } else {
+    const float x[4] = {v.x, v.y, v.z, v.w};
+    __nv_bfloat16 h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      h[i] = __float2bfloat16_rn(x[i]);
+      l[i] = __float2bfloat16_rn(__fsub_rn(x[i], __bfloat162float(h[i])));
+    }
+    *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(hi) + off) =
+        *reinterpret_cast<const uint2*>(h);
+    if (lo)
+      *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(lo) + off) =
+          *reinterpret_cast<const uint2*>(l);
   }
-  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kObThreads)
+k_operand_blocked(const float* __restrict__ src, int64_t rows, int64_t cols, int64_t lds,
+                  int transpose, int mode, void* __restrict__ hi, void* __restrict__ lo,
+                  int64_t nkb, int kbe, int vec) {
+  __shared__ float T[64 * kObLd];   // transposed copy: T[k][m]
+  const int64_t blk = blockIdx.x;
+  const int64_t mt = blk / nkb, kb = blk % nkb;
+  const int64_t m0 = mt * 128, k0 = kb * kbe;
   const int64_t M = transpose ? cols : rows, K = transpose ? rows : cols;
-  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-    int64_t m, k;
-    float v;
-    if (transpose) { m = c0 + y; k = r0 + threadIdx.x; v = t[threadIdx.x][y]; }
-    else           { m = r0 + y; k = c0 + threadIdx.x; v = t[y][threadIdx.x]; }
-    if (m >= M || k >= K) continue;
-    const int64_t off = (((m >> 7) * nkb + k / kbe) * 128 + (m & 127)) * kbe + (k % kbe);
-    if (mode == 1) {
-      static_cast<float*>(hi)[off] = round_tf32(v);
-    } else if (mode == 2) {
-      static_cast<float*>(hi)[off] = v;
-    } else {
-      const __nv_bfloat16 h = __float2bfloat16_rn(v);
-      static_cast<__nv_bfloat16*>(hi)[off] = h;
-      if (lo)
-        static_cast<__nv_bfloat16*>(lo)[off] =
-            __float2bfloat16_rn(__fsub_rn(v, __bfloat162float(h)));
+  const int kq = kbe / 4;                 // 4-value groups per output row
+  const int nq = 128 * kq;
+  const int64_t base = blk * 128 * (int64_t)kbe;
+  if (transpose) {
+    // source rows k0 .. k0+kbe-1 (K index), columns m0 .. m0+127 (M index)
+    for (int q = threadIdx.x; q < kbe * 32; q += kObThreads) {
+      const int kk = q >> 5, mq = (q & 31) * 4;
+      const int64_t k = k0 + kk;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k < K) v = load4(src + k * lds, m0 + mq, M, vec != 0);
+      float* t = &T[kk * kObLd + mq];
+      t[0] = v.x; t[1] = v.y; t[2] = v.z; t[3] = v.w;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int q = threadIdx.x; q < nq; q += kObThreads) {
+      const int mm = q / kq, kk = (q % kq) * 4;
+      float4 v;
+      v.x = T[(kk + 0) * kObLd + mm];
+      v.y = T[(kk + 1) * kObLd + mm];
+      v.z = T[(kk + 2) * kObLd + mm];
+      v.w = T[(kk + 3) * kObLd + mm];
+      store4(hi, lo, base + (int64_t)mm * kbe + kk, mode, v);
+    }
+  } else {
+#pragma unroll 4
+    for (int q = threadIdx.x; q < nq; q += kObThreads) {
+      const int mm = q / kq, kk = (q % kq) * 4;
+      const int64_t m = m0 + mm;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m < M) v = load4(src + m * lds, k0 + kk, K, vec != 0);
+      store4(hi, lo, base + (int64_t)mm * kbe + kk, mode, v);
     }
   }
 }
@@ -225,7 +223,9 @@ __global__ void k_gram_reduce(const float* __restrict__ part, int tiles, int r,
 // summed pairwise per thread (32 entries per tile), then in float64 across
 // tiles, then across threads and blocks in a fixed order.
 // Tile: 64 rows x 128 columns of V; 256 threads; thread (ty, tx) owns rows
-// ty + 8a (a < 8) and columns tx + 32b (b < 4).
+// ty + 8a (a < 8) and columns 4 tx + b (b < 4): 16-byte loads of V and H,
+// and per pair of ranks two 16-byte H loads and eight 8-byte W loads
+// (broadcast within the warp) for 64 FMAs.
 // ---------------------------------------------------------------------------
 constexpr int kObjBM = 64, kObjBN = 128, kObjThreads = 256, kObjBlocks = 1216;
 
@@ -241,12 +241,14 @@ k_objective(const float* __restrict__ V, int64_t ldv, const float* __restrict__ 
             double* __restrict__ partials) {
   extern __shared__ float sm[];
   const int rp = (r + 1) & ~1;               // even
-  float* Ws = sm;                            // [kObjBM][rp + 1]
-  float* Hs = sm + kObjBM * (rp + 1);        // [rp][kObjBN]
-  const int LW = rp + 1;
+  const int LW = rp;                         // W row stride (even: 8-byte loads)
+  float* Ws = sm;                            // [kObjBM][rp]
+  float* Hs = sm + kObjBM * rp;              // [rp][kObjBN]
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int64_t tiles_m = ceil_div(p, kObjBM), tiles_n = ceil_div(n, kObjBN);
   const int64_t ntiles = tiles_m * tiles_n;
+  const bool vec_v = (ldv % 4 == 0) && (reinterpret_cast<uintptr_t>(V) % 16 == 0);
+  const bool vec_h = (n % 4 == 0) && (reinterpret_cast<uintptr_t>(H) % 16 == 0);
   double acc64 = 0.0;
 
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -256,18 +258,41 @@ k_objective(const float* __restrict__ V, int64_t ldv, const float* __restrict__ 
       const int m = q / rp, k = q % rp;
       Ws[m * LW + k] = (i0 + m < p && k < r) ? W[(i0 + m) * r + k] : 0.f;
     }
-    for (int q = tid; q < rp * kObjBN; q += kObjThreads) {
-      const int k = q / kObjBN, c = q % kObjBN;
-      Hs[k * kObjBN + c] = (j0 + c < n && k < r) ? H[(int64_t)k * n + j0 + c] : 0.f;
+    for (int q = tid; q < rp * (kObjBN / 4); q += kObjThreads) {
+      const int k = q / (kObjBN / 4), c = (q % (kObjBN / 4)) * 4;
+      const int64_t j = j0 + c;
+      float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k < r) {
+        const float* src = H + (int64_t)k * n + j;
+        if (vec_h && j + 3 < n) {
+          h = *reinterpret_cast<const float4*>(src);
+        } else {
+          h.x = j < n ? src[0] : 0.f;
+          h.y = j + 1 < n ? src[1] : 0.f;
+          h.z = j + 2 < n ? src[2] : 0.f;
+          h.w = j + 3 < n ? src[3] : 0.f;
+        }
+      }
+      *reinterpret_cast<float4*>(&Hs[k * kObjBN + c]) = h;
     }
     float v[8][4];
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int64_t i = i0 + ty + 8 * a, j = j0 + tx + 32 * b;
-        v[a][b] = (i < p && j < n) ? __ldcs(V + i * ldv + j) : 0.f;
+    for (int a = 0; a < 8; ++a) {
+      const int64_t i = i0 + ty + 8 * a, j = j0 + 4 * tx;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < p) {
+        const float* src = V + i * ldv + j;
+        if (vec_v && j + 3 < n) {
+          x = __ldcs(reinterpret_cast<const float4*>(src));
+        } else {
+          x.x = j < n ? __ldcs(src) : 0.f;
+          x.y = j + 1 < n ? __ldcs(src + 1) : 0.f;
+          x.z = j + 2 < n ? __ldcs(src + 2) : 0.f;
+          x.w = j + 3 < n ? __ldcs(src + 3) : 0.f;
+        }
       }
+      v[a][0] = x.x; v[a][1] = x.y; v[a][2] = x.z; v[a][3] = x.w;
+    }
     __syncthreads();
     float s0[8][4], s1[8][4];
 #pragma unroll
@@ -275,24 +300,19 @@ k_objective(const float* __restrict__ V, int64_t ldv, const float* __restrict__ 
 #pragma unroll
       for (int b = 0; b < 4; ++b) { s0[a][b] = 0.f; s1[a][b] = 0.f; }
     for (int k = 0; k < rp; k += 2) {
-      float h0[4], h1[4], w0[8], w1[8];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        h0[b] = Hs[k * kObjBN + tx + 32 * b];
-        h1[b] = Hs[(k + 1) * kObjBN + tx + 32 * b];
-      }
+      const float4 h0 = *reinterpret_cast<const float4*>(&Hs[k * kObjBN + 4 * tx]);
+      const float4 h1 = *reinterpret_cast<const float4*>(&Hs[(k + 1) * kObjBN + 4 * tx]);
+      const float h0v[4] = {h0.x, h0.y, h0.z, h0.w};
+      const float h1v[4] = {h1.x, h1.y, h1.z, h1.w};
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
-        w0[a] = Ws[(ty + 8 * a) * LW + k];
-        w1[a] = Ws[(ty + 8 * a) * LW + k + 1];
-      }
-#pragma unroll
-      for (int a = 0; a < 8; ++a)
+        const float2 w = *reinterpret_cast<const float2*>(&Ws[(ty + 8 * a) * LW + k]);
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-          s0[a][b] = fmaf(w0[a], h0[b], s0[a][b]);
-          s1[a][b] = fmaf(w1[a], h1[b], s1[a][b]);
+          s0[a][b] = fmaf(w.x, h0v[b], s0[a][b]);
+          s1[a][b] = fmaf(w.y, h1v[b], s1[a][b]);
         }
+      }
     }
     float sq[32];
 #pragma unroll
@@ -350,39 +370,18 @@ cudaError_t launch_seed_uniform(float* dst, int64_t count, uint64_t seed, uint64
   return cudaGetLastError();
 }
 
-cudaError_t launch_copy_pad(const float* src, int64_t rows, int64_t cols, int64_t lds,
-                            float* dst, int64_t ldd, bool tf32, cudaStream_t st) {
-  k_copy_pad<<<grid_for(rows * ldd, 256), 256, 0, st>>>(src, rows, cols, lds, dst, ldd,
-                                                          tf32 ? 1 : 0);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_transpose_pad(const float* src, int64_t rows, int64_t cols, int64_t lds,
-                                 float* dst, int64_t ldd, bool tf32, cudaStream_t st) {
-  // dst columns run over src rows 0..ldd-1 (zero beyond rows)
-  dim3 grid((unsigned)ceil_div(cols, 32), (unsigned)ceil_div(ldd, 32));
-  k_transpose_pad<<<grid, dim3(32, 8), 0, st>>>(src, rows, cols, lds, dst, ldd, tf32 ? 1 : 0);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_split_bf16(const float* src, int64_t rows, int64_t cols, int64_t lds,
-                              bool transpose, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                              int64_t ldd, cudaStream_t st) {
-  // grid covers the padded output extent
-  const int64_t gr = transpose ? ldd : rows;
-  const int64_t gc = transpose ? cols : ldd;
-  dim3 grid((unsigned)ceil_div(gc, 32), (unsigned)ceil_div(gr, 32));
-  k_split_bf16<<<grid, dim3(32, 8), 0, st>>>(src, rows, cols, lds, transpose ? 1 : 0, hi, lo,
-                                              ldd);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_operand_blocked(const float* src, int64_t rows, int64_t cols, int64_t lds,
                                    bool transpose, int mode, void* hi, void* lo, int64_t nkb,
                                    int kbe, cudaStream_t st) {
-  dim3 grid((unsigned)ceil_div(cols, 32), (unsigned)ceil_div(rows, 32));
-  k_operand_blocked<<<grid, dim3(32, 8), 0, st>>>(src, rows, cols, lds, transpose ? 1 : 0, mode,
-                                                   hi, lo, nkb, kbe);
+  if (kbe % 4 != 0 || kbe > 64) return cudaErrorInvalidValue;
+  const int64_t M = transpose ? cols : rows;
+  const int64_t blocks = ceil_div(M, 128) * nkb;
+  if (blocks <= 0) return cudaSuccess;
+  if (blocks > INT32_MAX) return cudaErrorInvalidValue;
+  const int vec = (lds % 4 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0) ? 1 : 0;
+  k_operand_blocked<<<(unsigned)blocks, kObThreads, 0, st>>>(src, rows, cols, lds,
+                                                            transpose ? 1 : 0, mode, hi, lo, nkb,
+                                                            kbe, vec);
   return cudaGetLastError();
 }
 
@@ -425,7 +424,7 @@ cudaError_t launch_objective(const float* V, int64_t ldv, const float* W, const 
                              int64_t p, int64_t n, int r, double* partials, int nparts,
                              double* f_dev, cudaStream_t st) {
   const int rp = (r + 1) & ~1;
-  const size_t smem = ((size_t)kObjBM * (rp + 1) + (size_t)rp * kObjBN) * sizeof(float);
+  const size_t smem = ((size_t)kObjBM * rp + (size_t)rp * kObjBN) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(k_objective, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

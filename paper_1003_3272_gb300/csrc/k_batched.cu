@@ -299,9 +299,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(const BatchParams a)
   if (*(volatile int*)&s_abort && threadIdx.x == 0) atomicExch(a.err, (int)NMF_ETIMEOUT);
 }
 
-// Gram of the factor that the half step does not update, one block per
-// instance: float32 within 128-row windows, float64 across (tcepi::gram_rows),
-// then the padded float32 copy used by the epilogue.
+// Gram of the factor that the half step does not update, for every
+// instance: float32 within 128-row windows, float64 across them.  One block
+// per chunk of 256 rows of one instance (two windows, one per 64-thread
+// group, each thread a 4 x 4 block of the 32 x 32 Gram); the block's float64
+// partial goes to a workspace slot, and the instance's last block to finish
+// sums the slots in chunk order (fixed, so the result does not depend on
+// which block finishes last), then writes G64 and the padded float32 copy.
+constexpr int kGramChunk = 256;
+constexpr int kGramThreads = 128;
+constexpr int kGramLd = kBR + 4;
+
 struct GramInst {
   const float* Q;            // W (layout 0, ldq = r) or H (layout 1, ldq = n)
   int layout;
@@ -309,17 +317,78 @@ struct GramInst {
   int r;
   double* G64;               // r x r
   float* Gpad;               // kBR x kBR
+  int chunk0, nchunks;       // this instance's slots in the partial workspace
+  unsigned int* done;        // blocks finished; reset to 0 by the last one
 };
 
-__global__ void __launch_bounds__(192) k_batched_gram(const GramInst* gi) {
-  __shared__ __align__(16) float Qs[tcepi::kQsRows * tcepi::ldq<kBR>()];
-  const GramInst g = gi[blockIdx.x];
-  tcepi::gram_rows<kBR>(Qs, g.Q, g.layout, g.ldq, 0, g.QM, g.r, g.G64, threadIdx.x);
-  __threadfence_block();
+__global__ void __launch_bounds__(kGramThreads)
+k_batched_gram(const GramInst* gi, const int2* items, double* gpart) {
+  __shared__ __align__(16) float Qs[2][128][kGramLd];
+  __shared__ double red[64][16];
+  __shared__ int s_last;
+  const int2 it = items[blockIdx.x];
+  const GramInst g = gi[it.x];
+  const int t = threadIdx.x;
+  const int64_t row0 = (int64_t)(it.y - g.chunk0) * kGramChunk;
+  // stage 256 rows x kBR (zero beyond r and beyond QM)
+  for (int q = t; q < kGramChunk * kBR; q += kGramThreads) {
+    int m, k;
+    if (g.layout == 1) { k = q / kGramChunk; m = q % kGramChunk; }
+    else               { m = q / kBR; k = q % kBR; }
+    const int64_t row = row0 + m;
+    float v = 0.f;
+    if (k < g.r && row < g.QM)
+      v = g.layout == 1 ? g.Q[(int64_t)k * g.ldq + row] : g.Q[row * g.ldq + k];
+    Qs[m >> 7][m & 127][k] = v;
+  }
   __syncthreads();
-  for (int q = threadIdx.x; q < kBR * kBR; q += blockDim.x) {
-    const int l = q / kBR, k = q % kBR;
-    g.Gpad[q] = (l < g.r && k < g.r) ? (float)g.G64[l * g.r + k] : 0.f;
+  const int grp = t >> 6, bi = (t & 63) >> 3, bj = t & 7;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
+  for (int m = 0; m < 128; ++m) {
+    const float4 a = *reinterpret_cast<const float4*>(&Qs[grp][m][bi * 4]);
+    const float4 b = *reinterpret_cast<const float4*>(&Qs[grp][m][bj * 4]);
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+  if (grp == 1) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) red[t & 63][i * 4 + j] = (double)acc[i][j];
+  }
+  __syncthreads();
+  if (grp == 0) {
+    double* dst = gpart + (int64_t)it.y * kBR * kBR;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        dst[(bi * 4 + i) * kBR + bj * 4 + j] = (double)acc[i][j] + red[t][i * 4 + j];
+  }
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(g.done, 1u) == (unsigned)(g.nchunks - 1);
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    for (int q = t; q < kBR * kBR; q += kGramThreads) {
+      const int k = q / kBR, l = q % kBR;
+      double sum = 0.0;
+      for (int c = 0; c < g.nchunks; ++c)
+        sum += __ldcg(gpart + (int64_t)(g.chunk0 + c) * kBR * kBR + q);
+      if (k < g.r && l < g.r) g.G64[k * g.r + l] = sum;
+      g.Gpad[q] = (k < g.r && l < g.r) ? (float)sum : 0.f;
+    }
+    if (t == 0) *g.done = 0u;
   }
   // the next kernel may be scheduled; it waits for this grid before reading
   ptx::pdl_launch_dependents();
@@ -488,6 +557,10 @@ struct nmf_batch {
   int* d_off[2] = {nullptr, nullptr};
   int grid[2] = {0, 0};
   GramInst* d_gram[2] = {nullptr, nullptr};
+  int2* d_gitems[2] = {nullptr, nullptr};   // (instance, chunk) per Gram block
+  int gblocks[2] = {0, 0};
+  double* d_gpart = nullptr;                 // per-chunk float64 partials
+  unsigned int* d_gdone = nullptr;           // [2][count] finished-block counters
   ObjInst* d_obj = nullptr;
   int* d_tile_inst = nullptr;
   int obj_tiles = 0;
@@ -574,7 +647,8 @@ cudaError_t launch_batched_tc(nmf_batch* b, int half) {
 
 cudaError_t launch_half(nmf_batch* b, int half) {
   // Gram of the other factor: half 0 (H update) needs W^T W, half 1 needs H H^T
-  k_batched_gram<<<b->count, 192, 0, b->st>>>(b->d_gram[half]);
+  k_batched_gram<<<b->gblocks[half], kGramThreads, 0, b->st>>>(b->d_gram[half],
+                                                                 b->d_gitems[half], b->d_gpart);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   count_launches(2);
@@ -713,9 +787,34 @@ nmf_status nmf_batched_init(int count, const nmf_config* cfgs, const float* cons
       nmf_batched_destroy(b);
       return bfail(nullptr, NMF_ECUDA, "tensor map encoding failed");
     }
-    gram[0][i] = GramInst{W[i], 0, r, p, r, gw64, gwp};
-    gram[1][i] = GramInst{H[i], 1, n, n, r, gh64, ghp};
+    gram[0][i] = GramInst{W[i], 0, r, p, r, gw64, gwp, 0, 0, nullptr};
+    gram[1][i] = GramInst{H[i], 1, n, n, r, gh64, ghp, 0, 0, nullptr};
   }
+  // Gram blocks: chunks of 256 rows, numbered across both halves so that
+  // each has its own partial slot
+  std::vector<int2> gitems[2];
+  int nslots = 0;
+  if ((e = balloc(b, (void**)&b->d_gdone, sizeof(unsigned int) * 2 * count)) != cudaSuccess)
+    return fail_cuda(e, "cudaMalloc");
+  for (int h = 0; h < 2; ++h) {
+    for (int i = 0; i < count; ++i) {
+      GramInst& g = gram[h][i];
+      g.chunk0 = nslots;
+      g.nchunks = (int)ceil_div(g.QM, kGramChunk);
+      g.done = b->d_gdone + h * count + i;
+      for (int c = 0; c < g.nchunks; ++c) gitems[h].push_back(make_int2(i, nslots + c));
+      nslots += g.nchunks;
+    }
+    b->gblocks[h] = (int)gitems[h].size();
+  }
+  if ((e = balloc(b, (void**)&b->d_gpart, sizeof(double) * kBR * kBR * (size_t)nslots)) != cudaSuccess ||
+      (e = balloc(b, (void**)&b->d_gitems[0], sizeof(int2) * gitems[0].size())) != cudaSuccess ||
+      (e = balloc(b, (void**)&b->d_gitems[1], sizeof(int2) * gitems[1].size())) != cudaSuccess)
+    return fail_cuda(e, "cudaMalloc");
+  cudaMemcpyAsync(b->d_gitems[0], gitems[0].data(), sizeof(int2) * gitems[0].size(),
+                  cudaMemcpyHostToDevice, b->st);
+  cudaMemcpyAsync(b->d_gitems[1], gitems[1].data(), sizeof(int2) * gitems[1].size(),
+                  cudaMemcpyHostToDevice, b->st);
   // device tables
   if ((e = balloc(b, (void**)&b->d_inst, sizeof(BatchInst) * count)) != cudaSuccess ||
       (e = balloc(b, (void**)&b->d_maps, sizeof(CUtensorMap) * maps.size())) != cudaSuccess ||

@@ -144,3 +144,13 @@ def test_tall_sweep_objective_20_iterations(tall_v, prec, r):
     fo = _golden_objective(f"tall_65536x4096_r{r}", 20)
     f = _gpu_objective(pr, prec, 20)
     assert abs(f - fo) / fo <= TRAJ_BAR[prec], (prec, r, f, fo)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_large_streaming_objective_20_iterations(large_v, prec):
+    c = synth.LARGE
+    W0, H0 = synth.starting_factors(synth.BASE_SEED + 4, c["p"], c["n"], c["r"])
+    pr = synth.Problem("large", large_v, W0, H0, c["r"], 20, 1e-10, synth.BASE_SEED + 4)
+    fo = _golden_objective("large_131072x16384_r64", 20)
+    f = _gpu_objective(pr, prec, 20)
+    assert abs(f - fo) / fo <= TRAJ_BAR[prec], (prec, f, fo)

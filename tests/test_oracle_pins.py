@@ -393,3 +393,25 @@ def _mutant_steps():
 def test_planted_mistakes_fail_the_exact_pin(mutant):
     assert _golden_check(lambda V, W, H: orc.step(V, W, H, 0.0))      # the oracle passes
     assert not _golden_check(mutant)                                   # the mutant does not
+
+
+def test_stored_objective_trajectories():
+    """tests/golden/objectives.json (the oracle's trajectories on the measured
+    workloads): every stored trajectory descends (the MM property), and the
+    small workloads' entries reproduce from the oracle here."""
+    import json
+    with open(os.path.join(GOLDEN, "objectives.json")) as fh:
+        d = json.load(fh)
+    for name, e in d.items():
+        if name.startswith("_"):
+            continue
+        ks = sorted(int(k) for k in e["objective"])
+        fs = [e["objective"][str(k)] for k in ks]
+        assert all(b <= a for a, b in zip(fs, fs[1:])), name
+    pr = synth.faces()
+    W, H, _, _ = orc.run(pr.V, pr.W0, pr.H0, 10, eps=pr.eps)
+    assert orc.objective(pr.V, W, H) == pytest.approx(
+        d["faces_361x2429_r10"]["objective"]["10"], rel=1e-12)
+    pr = synth.planted(p=1024, n=1024, r=50, iters=10)
+    assert orc.objective(pr.V, pr.W0, pr.H0) == pytest.approx(
+        d["planted_1024x1024_r50"]["objective"]["0"], rel=1e-12)
