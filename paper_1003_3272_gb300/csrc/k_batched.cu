@@ -2,9 +2,10 @@
 // problems (Section 3.1, Eqs. (3.3)-(3.4)) updated together.
 //
 // Per half step of every instance b (H update, then W update):
-//   k_batched_gram : one block per instance forms the r_b x r_b Gram of the
-//                    factor that is *not* updated (float32 within 128-row
-//                    windows, float64 across them, fixed order).
+//   k_batched_gram : the r_b x r_b Gram of the factor that is *not* updated,
+//                    one block per 256-row chunk of each instance (float32
+//                    within 128-row windows, float64 across them, summed in
+//                    chunk order by the instance's last block).
 //   k_batched_tc   : a persistent grid walks a host-scheduled list of
 //                    (instance, 128-row tile) items; per item the whole K
 //                    range of the tile is streamed (TMA, tile-blocked V
