@@ -182,6 +182,19 @@ void nmf_batched_destroy(nmf_batch* b);
 nmf_status nmf_gram_noalloc(const float* F, int32_t layout, int64_t M, int64_t ldf, int32_t r,
                             double* G_out, void* stream);
 
+/* ---- Self-check of the update's division ----------------------------------
+ * No counterpart in the paper.  The update new = (old * num) / (den + eps)
+ * (Eqs. (3.3)-(3.4)) divides with IEEE round-to-nearest; the kernels do so by
+ * Markstein's quotient correction where its conditions hold and by the IEEE
+ * division elsewhere.  This runs `count` divisions on the current device
+ * (the first 64 * 2^23 sweep every significand of the divisor against 64
+ * dividends; the rest are random operand pairs drawn from `seed`) and
+ * reports how many differ bit for bit from the IEEE division
+ * (*mismatches) and how many took the quick form (*quick).  Synchronous;
+ * allocates 16 bytes.  NMF_EINVAL for count < 0 or null outputs.           */
+nmf_status nmf_selfcheck_div(int64_t count, uint64_t seed, uint64_t* mismatches,
+                             uint64_t* quick);
+
 /* ---- Instrumentation ---------------------------------------------------
  * Number of kernels this library has launched in this process (all
  * contexts), for launch accounting.                                         */

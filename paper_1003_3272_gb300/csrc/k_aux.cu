@@ -434,3 +434,73 @@ cudaError_t launch_objective(const float* V, int64_t ldv, const float* W, const 
 }
 
 }  // namespace nmf
+
+// ---------------------------------------------------------------------------
+// Self-check of div_rn against the IEEE division: case i < 2^23 * nx sweeps
+// every significand of d in [1, 2) against nx significands of x (drawn from
+// the counter generator, with exponents spread over the quick range); the
+// remaining cases draw both operands at random (x = 0 included).
+// ---------------------------------------------------------------------------
+namespace nmf {
+namespace {
+
+__global__ void k_selfcheck_div(uint64_t key, int64_t count, int nx,
+                                unsigned long long* mismatches, unsigned long long* quick) {
+  unsigned long long bad = 0, fast = 0;
+  const int64_t sweep = (int64_t)nx << 23;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t bx, bd;
+    if (i < sweep) {
+      const uint64_t w = mix64(key + (uint64_t)(i >> 23) * kGolden);
+      const uint32_t ex = 64u + (uint32_t)(w % 127u);          // 2^-63 .. 2^63
+      bx = (ex << 23) | (uint32_t)((w >> 20) & 0x7fffffu);
+      const uint32_t ed = 64u + (uint32_t)((w >> 50) % 127u);
+      bd = (ed << 23) | (uint32_t)(i & 0x7fffff);
+    } else {
+      const uint64_t w = mix64(key + (uint64_t)(i + 1) * kGolden);
+      bx = (uint32_t)(1u + (w % 253u)) << 23 | (uint32_t)((w >> 8) & 0x7fffffu);
+      bd = (uint32_t)(1u + ((w >> 32) % 253u)) << 23 | (uint32_t)((w >> 40) & 0x7fffffu);
+      if ((w & 0xffu) == 0u) bx = 0u;
+    }
+    const float x = __uint_as_float(bx), d = __uint_as_float(bd);
+    const float a = div_rn(x, d), b = __fdiv_rn(x, d);
+    if (__float_as_uint(a) != __float_as_uint(b)) ++bad;
+    if (div_rn_quick_ok(x, d)) ++fast;
+  }
+  if (bad) atomicAdd(mismatches, bad);
+  atomicAdd(quick, fast);
+}
+
+}  // namespace
+}  // namespace nmf
+
+extern "C" nmf_status nmf_selfcheck_div(int64_t count, uint64_t seed, uint64_t* mismatches,
+                                        uint64_t* quick) {
+  using namespace nmf;
+  if (count < 0 || !mismatches || !quick) {
+    record_error("nmf_selfcheck_div: count must be >= 0 and the outputs non-null");
+    return NMF_EINVAL;
+  }
+  unsigned long long* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, 2 * sizeof(unsigned long long));
+  if (e != cudaSuccess) { record_error("nmf_selfcheck_div: cudaMalloc failed"); return NMF_ENOMEM; }
+  unsigned long long h[2] = {0, 0};
+  e = cudaMemset(d, 0, sizeof(h));
+  const int nx = 64;
+  if (e == cudaSuccess) {
+    k_selfcheck_div<<<1216, 256>>>(mix64(seed), count, nx, d, d + 1);
+    count_launches(1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    record_error(cudaGetErrorString(e));
+    return NMF_ECUDA;
+  }
+  *mismatches = h[0];
+  *quick = h[1];
+  return NMF_OK;
+}
+

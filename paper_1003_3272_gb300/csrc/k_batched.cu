@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(const BatchParams a)
           for (int l = 0; l < kBR; ++l)
             if (l < r) den = fmaf(old[l], Gs[l * kBR + k], den);
           den = __fadd_rn(den, B.eps);
-          const float v = __fdiv_rn(__fmul_rn(old[k], num[k]), den);
+          const float v = div_rn(__fmul_rn(old[k], num[k]), den);
           if (half == 0) F[(int64_t)k * ldf + m] = v;
           else           F[m * ldf + k] = v;
           plane_store(B.plane, B.op_hi[half], B.op_lo[half], (int64_t)k * B.ldop[half] + m, v);

@@ -1,36 +1,41 @@
 // Tensor-core (tcgen05) form of the two V-streaming products of an MM
 // iteration (Section 3.1: the numerators V H^T of Eq. (3.3) and W^T V of
-// Eq. (3.4)), for the TF32, split-BF16x3 and BF16 precisions, with the
-// multiply-divide update fused behind them.
+// Eq. (3.4)), for the TF32, split-BF16x3 and BF16 precisions, with the Gram
+// of the other factor and the multiply-divide update fused into the same
+// launch: one launch per half step.
 //
-// Both products are D[M x r] = X[M x K] . Y[r x K]^T with X and Y K-major
-// (see k_stream_simt.cu for the operand roles).
+// Both products are D[M x r] = X[M x K] . Y[r x K]^T with X and Y K-major:
+// the H update has X = V^T (M = n, K = p) and Y = W^T, the W update X = V
+// (M = p, K = n) and Y = H.  X is read from a tile-blocked copy (blocks of
+// 128 rows x 128 bytes of K stored contiguously), Y from the factor's
+// operand plane.
 //
-// Work decomposition.  A thread-block cluster of S blocks (S = 1, 2, 4, 8)
-// owns one 128-row tile of X at a time and splits its K range evenly; the
-// grid is persistent (at most the co-resident number of clusters) and a
-// cluster walks the tiles g, g + G, g + 2G, ...  Per block:
-//   warp 0, one lane : TMA producer.  A stage holds 128 bytes of K (64 bf16
-//                      or 32 tf32 values) of the X tile (128 rows) and of
-//                      the Y tile (RPAD rows), 128-byte swizzled.
+// Work decomposition.  A thread-block cluster of S blocks (S = 2, 4, 8) owns
+// one 128-row tile of X at a time and splits its K range evenly; the grid is
+// persistent (at most the co-resident number of clusters) and a cluster
+// walks the tiles g, g + G, g + 2G, ...  Per block (256 threads):
+//   warp 0, one lane : TMA producer.  A stage holds 128 (or 64) bytes of K of
+//                      the X tile (128 rows) and of the Y tile (RPAD rows),
+//                      swizzled to the stage width.
 //   warp 1, one lane : MMA issuer, tcgen05.mma M=128, N=RPAD, 32 bytes of K
-//                      per instruction, float32 accumulator in tensor memory;
-//                      BF16x3 issues hi*hi + hi*lo + lo*hi.
-//   warps 2-3        : in the prologue, this block's share of the Gram matrix
-//                      of the *other* factor (float64 sum of the previous
-//                      half step's per-slice partials, fixed order), published
-//                      through a grid-wide counter.
-//   all 4 warps      : tile epilogue -- accumulator to shared memory; the
-//                      cluster reduces the S partial tiles over distributed
-//                      shared memory in rank order (deterministic), each block
-//                      taking 128/S rows; then the fused multiply-divide update
-//                      of its rows, the operand planes of the new factor and
-//                      the rows' partial Gram.
+//                      per instruction, float32 accumulators in tensor
+//                      memory; BF16x3 issues hi*hi + hi*lo + lo*hi.
+//   warps 2-7        : helpers (tc_epi.cuh).  Prologue: the Gram of the
+//                      other factor (per-block partials, grid-wide counter,
+//                      fixed-order float64 reduction, counter).  During the
+//                      stream: the old rows of this block's slice and the
+//                      denominators old . G.
+//   after the stream : accumulators to shared memory; the cluster sums its S
+//                      partial tiles over distributed shared memory in rank
+//                      order (deterministic), each block taking 128/S rows;
+//                      then the update (IEEE multiply and divide) and the new
+//                      factor's operand planes.
 // Every wait is bounded: on a timeout the block records NMF_ETIMEOUT in the
 // error word, lets its copies and MMAs drain, frees its tensor memory and
 // returns.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 
@@ -76,15 +81,26 @@ struct TcParams {
 
 template <int PREC>
 struct PrecTraits;
-template <> struct PrecTraits<NMF_TF32>   { static constexpr int XPL = 1, KB = 32, FMT = 2; };
-template <> struct PrecTraits<NMF_BF16X3> { static constexpr int XPL = 2, KB = 64, FMT = 1; };
-template <> struct PrecTraits<NMF_BF16>   { static constexpr int XPL = 1, KB = 64, FMT = 1; };
+template <> struct PrecTraits<NMF_TF32>   { static constexpr int XPL = 1, FMT = 2; };
+template <> struct PrecTraits<NMF_BF16X3> { static constexpr int XPL = 2, FMT = 1; };
+template <> struct PrecTraits<NMF_BF16>   { static constexpr int XPL = 1, FMT = 1; };
+
+// Bytes of K per stage: 128 (one block of the blocked copy), or 64 for split
+// BF16x3 at ranks above 64, whose 128-byte stages (4 planes) would leave
+// room for only two in shared memory; 64-byte stages (64-byte swizzle) give
+// five.
+template <int PREC, int RPAD>
+__host__ __device__ constexpr int stage_kbytes() {
+  return (PREC == NMF_BF16X3 && RPAD >= 80) ? 64 : 128;
+}
 
 template <int PREC, int RPAD>
 struct TcShape {
   static constexpr int XPL = PrecTraits<PREC>::XPL;
-  static constexpr int X_BYTES = kBM * 128;       // one plane of X: 128 rows x 128 B
-  static constexpr int Y_BYTES = RPAD * 128;      // one plane of Y
+  static constexpr int KBY = stage_kbytes<PREC, RPAD>();
+  static constexpr int KB = KBY / (PREC == NMF_TF32 ? 4 : 2);   // K elements per stage
+  static constexpr int X_BYTES = kBM * KBY;       // one plane of X: 128 rows x KBY
+  static constexpr int Y_BYTES = RPAD * KBY;      // one plane of Y
   static constexpr int STAGE = XPL * (X_BYTES + Y_BYTES);
   static constexpr int LDA = RPAD + 4;            // accumulator tile row stride (floats)
   static constexpr int ACC = kBM * LDA * 4;       // partial accumulator tile
@@ -125,7 +141,8 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
             const TcParams a) {
   using Sh = TcShape<PREC, RPAD>;
   constexpr int STAGES = Sh::STAGES;
-  constexpr int KB = PrecTraits<PREC>::KB;
+  constexpr int KB = Sh::KB;
+  constexpr int KPB = 128 / Sh::KBY;   // stages per block of the blocked copy
   constexpr bool X3 = PREC == NMF_BF16X3;
   constexpr uint32_t IDESC = ptx::idesc(PrecTraits<PREC>::FMT, kBM, RPAD);
   constexpr int LDA = Sh::LDA;
@@ -152,9 +169,12 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
   // helpers' dedicated region: Qs | Os; denominators in the helpers' registers
   float* Qs = reinterpret_cast<float*>(smem + Sh::MAIN);
   float* Os = Qs + tcepi::kQsRows * tcepi::ldq<RPAD>();
-  tcepi::DenTile<RPAD> den;
+  tcepi::DenFor<RPAD> den;
 
   auto x_addr = [&](int s, int plane) { return sbase + s * Sh::STAGE + plane * Sh::X_BYTES; };
+  auto sdesc = [](uint32_t addr) {
+    return Sh::KBY == 128 ? ptx::sdesc_sw128(addr) : ptx::sdesc_sw64(addr);
+  };
   auto y_addr = [&](int s, int plane) {
     return sbase + s * Sh::STAGE + Sh::XPL * Sh::X_BYTES + plane * Sh::Y_BYTES;
   };
@@ -240,9 +260,11 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
         for (int kb = 0; kb < pre; ++kb) {
           const uint32_t fb = ptx::smem_u32(&full_bar[kb]);
           ptx::mbar_expect_tx(fb, Sh::STAGE);
-          const int32_t xb = (int32_t)((int64_t)tile * a.nkbt + kbeg / KB + kb);
-          ptx::tma_load_3d(x_addr(kb, 0), &tx_hi, 0, 0, xb, fb);
-          if (X3) ptx::tma_load_3d(x_addr(kb, 1), &tx_lo, 0, 0, xb, fb);
+          const int64_t hk = kbeg / KB + kb;
+          const int32_t xb = (int32_t)((int64_t)tile * a.nkbt + hk / KPB);
+          const int32_t xk = (int32_t)(hk % KPB) * KB;
+          ptx::tma_load_3d(x_addr(kb, 0), &tx_hi, xk, 0, xb, fb);
+          if (X3) ptx::tma_load_3d(x_addr(kb, 1), &tx_lo, xk, 0, xb, fb);
         }
         ptx::pdl_wait();
         // Our own predecessor is complete: the next half step may now be
@@ -269,10 +291,12 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
         const uint32_t fb = ptx::smem_u32(&full_bar[s]);
         ptx::mbar_expect_tx(fb, Sh::STAGE);
         const int32_t kc = (int32_t)(kbeg + (int64_t)kb * KB);
-        // X block (tile, k-block) of the tile-blocked copy: one contiguous 16 KB
-        const int32_t xb = (int32_t)((int64_t)tile * a.nkbt + kbeg / KB + kb);
-        ptx::tma_load_3d(x_addr(s, 0), &tx_hi, 0, 0, xb, fb);
-        if (X3) ptx::tma_load_3d(x_addr(s, 1), &tx_lo, 0, 0, xb, fb);
+        // X block (tile, k-block) of the tile-blocked copy (or its half)
+        const int64_t hk = kbeg / KB + kb;
+        const int32_t xb = (int32_t)((int64_t)tile * a.nkbt + hk / KPB);
+        const int32_t xk = (int32_t)(hk % KPB) * KB;
+        ptx::tma_load_3d(x_addr(s, 0), &tx_hi, xk, 0, xb, fb);
+        if (X3) ptx::tma_load_3d(x_addr(s, 1), &tx_lo, xk, 0, xb, fb);
         ptx::tma_load_2d(y_addr(s, 0), &ty_hi, kc, 0, fb);
         if (X3) ptx::tma_load_2d(y_addr(s, 1), &ty_lo, kc, 0, fb);
         issued = kb + 1;
@@ -305,9 +329,9 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
         if (*(volatile int*)&s_abort) break;
         ptx::tc_fence_after();
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t ah = ptx::sdesc_sw128(x_addr(s, 0) + kk * 32);
-          const uint64_t bh = ptx::sdesc_sw128(y_addr(s, 0) + kk * 32);
+        for (int kk = 0; kk < Sh::KBY / 32; ++kk) {
+          const uint64_t ah = sdesc(x_addr(s, 0) + kk * 32);
+          const uint64_t bh = sdesc(y_addr(s, 0) + kk * 32);
           const uint32_t tacc = tmem + (uint32_t)(ai * Sh::CS);
           const uint32_t acc = (kb >= a.nacc || kk != 0) ? 1u : 0u;
           if (PREC == NMF_TF32) {
@@ -315,8 +339,8 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
           } else {
             ptx::mma_bf16(tacc, ah, bh, IDESC, acc);
             if (X3) {
-              const uint64_t al = ptx::sdesc_sw128(x_addr(s, 1) + kk * 32);
-              const uint64_t bl = ptx::sdesc_sw128(y_addr(s, 1) + kk * 32);
+              const uint64_t al = sdesc(x_addr(s, 1) + kk * 32);
+              const uint64_t bl = sdesc(y_addr(s, 1) + kk * 32);
               ptx::mma_bf16(tcross, ah, bl, IDESC, (kb | kk) != 0);
               ptx::mma_bf16(tcross, al, bh, IDESC, 1);
             }
@@ -437,20 +461,21 @@ EncodeTiled get_encode() {
 }
 
 // 2-D K-major map: inner dimension K (elements), outer `rows`, row pitch
-// ld elements; box = 128 bytes of K x box_rows rows, 128-byte swizzle,
-// zero fill outside the tensor.
+// ld elements; box = kbytes (128 or 64) bytes of K x box_rows rows, swizzle
+// of the same width, zero fill outside the tensor.
 bool make_map(CUtensorMap* map, const void* base, bool bf16, int64_t K, int64_t rows, int64_t ld,
-              int box_rows, std::string* err) {
+              int box_rows, std::string* err, int kbytes = 128) {
   EncodeTiled enc = get_encode();
   if (!enc) { if (err) *err = "cuTensorMapEncodeTiled unavailable"; return false; }
   const int esz = bf16 ? 2 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ld * esz)};
-  cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)(kbytes / esz), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                    2, const_cast<void*>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   kbytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     if (err) *err = "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")";
@@ -460,20 +485,22 @@ bool make_map(CUtensorMap* map, const void* base, bool bf16, int64_t K, int64_t 
 }
 
 // 3-D map over a tile-blocked copy: blocks of 128 rows x 128 bytes stored
-// contiguously, `nblocks` of them; box = one block.
+// contiguously, `nblocks` of them; box = one block (kbytes = 128) or its
+// left or right half (kbytes = 64, 64-byte swizzle).
 bool make_map_blocked(CUtensorMap* map, const void* base, bool bf16, int64_t nblocks,
-                      std::string* err) {
+                      std::string* err, int kbytes = 128) {
   EncodeTiled enc = get_encode();
   if (!enc) { if (err) *err = "cuTensorMapEncodeTiled unavailable"; return false; }
   const int esz = bf16 ? 2 : 4;
   const int kbe = 128 / esz;
   cuuint64_t dims[3] = {(cuuint64_t)kbe, 128, (cuuint64_t)nblocks};
   cuuint64_t strides[2] = {128, 128 * 128};
-  cuuint32_t box[3] = {(cuuint32_t)kbe, 128, 1};
+  cuuint32_t box[3] = {(cuuint32_t)(kbytes / esz), 128, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                    3, const_cast<void*>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   kbytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     if (err) *err = "cuTensorMapEncodeTiled (blocked) failed (code " + std::to_string((int)r) + ")";
@@ -547,7 +574,11 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
   // float32 FMA path: ranks padded to 8; tensor cores: N granularity 16
   pl.rpad = prec == NMF_FP32 ? (int)round_up(r, 8) : rank_pad16(r);
   pl.block_m = kBM;
-  pl.kblock = (prec == NMF_TF32 || prec == NMF_FP32) ? 32 : 64;
+  // K elements per pipeline stage: 128 bytes, or 64 for split BF16x3 at
+  // ranks above 64 (see stage_kbytes)
+  const int kbytes = (prec == NMF_BF16X3 && pl.rpad >= 80) ? 64 : 128;
+  const int esz = (prec == NMF_TF32 || prec == NMF_FP32) ? 4 : 2;
+  pl.kblock = kbytes / esz;
   pl.M = M; pl.K = K; pl.r = r;
   pl.tiles = (int)ceil_div(M, kBM);
   if (M > INT32_MAX || K > INT32_MAX) { if (err) *err = "size exceeds TMA coordinates"; return NMF_EINVAL; }
@@ -564,8 +595,16 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
   }
   pl.smem = smem;
   const int64_t nkb = ceil_div(K, pl.kblock);
-  // Choose the cluster size S: fewest rounds of K/S work per block, then the
-  // most blocks at work.
+  // Choose the cluster size S by a time model: a block's share of a tile,
+  // ceil(nkb / S) stages at its share of HBM bandwidth (or, for the float32
+  // form, at about half its FMA rate), plus the tile epilogue (cluster
+  // reduction and update, a few microseconds growing with the rank), times
+  // the rounds of tiles; ties go to the most blocks at work.
+  const int xpl = prec == NMF_BF16X3 ? 2 : 1;
+  double stage_us = 128.0 * kbytes * xpl / 44000.0;   // ~6.7 TB/s over 152 SMs
+  if (prec == NMF_FP32)
+    stage_us = std::max(stage_us, 128.0 * pl.kblock * pl.rpad / (128.0 * 1900.0 * 0.5));
+  const double epi_us = 3.0 + pl.rpad / 16.0;
   int bestS = 0, bestG = 0;
   double best_cost = 1e300;
   int want = user_split;
@@ -584,7 +623,7 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
     if (maxc < 1) continue;
     const int G = maxc < pl.tiles ? maxc : pl.tiles;
     const int rounds = (int)ceil_div(pl.tiles, G);
-    const double cost = (double)rounds * (double)ceil_div(nkb, S) + 0.25 * rounds;
+    const double cost = (double)rounds * ((double)ceil_div(nkb, S) * stage_us + epi_us);
     if (cost < best_cost - 1e-9 || (cost < best_cost + 1e-9 && G * S > bestG * bestS)) {
       best_cost = cost;
       bestS = S;
@@ -609,7 +648,7 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
     const int cs = pl.rpad <= 32 ? 32 : (pl.rpad <= 64 ? 64 : 128);
     const int cross = prec == NMF_BF16X3 ? 1 : 0;
     const int amax = (512 / cs - cross) < 8 ? 512 / cs - cross : 8;
-    const int64_t adds = (pl.kchunk / pl.kblock) * 4;
+    const int64_t adds = (pl.kchunk / pl.kblock) * (kbytes / 32);   // MMAs per stage
     int na = (int)ceil_div(adds, 256);
     pl.nacc = na < 1 ? 1 : (na > amax ? amax : na);
     int cols = 32;
@@ -618,13 +657,14 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
   }
   const bool bf = prec == NMF_BF16X3 || prec == NMF_BF16;
   (void)ldx;
-  pl.nkbt = (int)nkb;
-  const int64_t nblocks = (int64_t)pl.tiles * nkb;
-  if (!make_map_blocked(&pl.x_hi, X_hi, bf, nblocks, err)) return NMF_ECUDA;
-  if (!make_map(&pl.y_hi, Y_hi, bf, K, r, ldy, pl.rpad, err)) return NMF_ECUDA;
+  // blocks of the blocked copy (128 bytes of K each) per tile row
+  pl.nkbt = (int)ceil_div(K, (int64_t)(128 / esz));
+  const int64_t nblocks = (int64_t)pl.tiles * pl.nkbt;
+  if (!make_map_blocked(&pl.x_hi, X_hi, bf, nblocks, err, kbytes)) return NMF_ECUDA;
+  if (!make_map(&pl.y_hi, Y_hi, bf, K, r, ldy, pl.rpad, err, kbytes)) return NMF_ECUDA;
   if (prec == NMF_BF16X3) {
-    if (!make_map_blocked(&pl.x_lo, X_lo, bf, nblocks, err)) return NMF_ECUDA;
-    if (!make_map(&pl.y_lo, Y_lo, bf, K, r, ldy, pl.rpad, err)) return NMF_ECUDA;
+    if (!make_map_blocked(&pl.x_lo, X_lo, bf, nblocks, err, kbytes)) return NMF_ECUDA;
+    if (!make_map(&pl.y_lo, Y_lo, bf, K, r, ldy, pl.rpad, err, kbytes)) return NMF_ECUDA;
   } else {
     pl.x_lo = pl.x_hi;
     pl.y_lo = pl.y_hi;

@@ -17,6 +17,8 @@
 // and writes the factor and its operand plane(s).
 #pragma once
 
+#include <type_traits>
+
 #include "epilogue.cuh"
 
 namespace nmf {
@@ -56,6 +58,47 @@ struct DenTile {
         for (int j = 0; j < 8; ++j) d[a][i][j] = 0.f;
   }
 };
+
+// Denominators for ranks above 64: one 8 x 8 block per helper thread, rows
+// mg*8 .. mg*8+7 and ranks kg*8 .. kg*8+7 (thread h: kg = h % KG, mg = h / KG),
+// so that each rank of G read from shared memory feeds 8 rows.
+template <int RPAD, int NH = kHelpers>
+struct DenTile8 {
+  static constexpr int KG = RPAD / 8;
+  static constexpr int MG = kRmax / 8;
+  static_assert(KG * MG <= NH, "one 8 x 8 block per helper");
+  float d[8][8];
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) d[i][j] = 0.f;
+  }
+};
+
+template <int RPAD, int NH = kHelpers>
+using DenFor = typename std::conditional<(RPAD > 64), DenTile8<RPAD, NH>, DenTile<RPAD, NH>>::type;
+
+// new = (old * num) / (den + eps) for 8 entries at once: the quick
+// correctly rounded divisions first (independent, so they overlap), then the
+// IEEE division for any entry outside the quick form's range.
+__device__ __forceinline__ void update8(const float* old, const float* num, const float* den,
+                                        float eps, float* v) {
+  float x[8], d[8];
+  bool slow = false;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    x[j] = __fmul_rn(old[j], num[j]);
+    d[j] = __fadd_rn(den[j], eps);
+    slow |= !div_rn_quick_ok(x[j], d[j]);
+    v[j] = div_rn_quick(x[j], d[j]);
+  }
+  if (slow) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (!div_rn_quick_ok(x[j], d[j])) v[j] = __fdiv_rn(x[j], d[j]);
+  }
+}
 
 template <int NH = kHelpers>
 __device__ __forceinline__ void helper_sync() {
@@ -105,8 +148,8 @@ struct RowStage {
 // rows (passes until every block is done); rows are staged 32 at a time,
 // the next 32 loaded into registers while the current ones are multiplied.
 template <int RPAD, int NH = kHelpers>
-__device__ void gram_rows(float* Qs, const float* Q, int layout, int64_t ldq_g, int64_t q0,
-                          int64_t q1, int r, double* gpart, int h) {
+__device__ void gram_rows4(float* Qs, const float* Q, int layout, int64_t ldq_g, int64_t q0,
+                           int64_t q1, int r, double* gpart, int h) {
   constexpr int LQ = ldq<RPAD>();
   const int nbr = (r + 3) / 4;
   const int npairs = nbr * (nbr + 1) / 2;
@@ -167,6 +210,95 @@ __device__ void gram_rows(float* Qs, const float* Q, int layout, int64_t ldq_g, 
     }
     helper_sync<NH>();            // Qs free for the next pass
   }
+}
+
+// The same partial Gram with one 8 x 8 block per thread (kb <= lb) in a
+// single pass, for ranks whose 4 x 4 blocks would need several passes: four
+// 16-byte loads per 64 FMAs.  The float64 window sums accumulate in the
+// thread's own entries of gpart (read-modify-write by that thread only), so
+// they take no registers.  Needs (ceil(r/8) (ceil(r/8) + 1) / 2) <= NH.
+template <int RPAD, int NH = kHelpers>
+__device__ void gram_rows8(float* Qs, const float* Q, int layout, int64_t ldq_g, int64_t q0,
+                           int64_t q1, int r, double* gpart, int h) {
+  constexpr int LQ = ldq<RPAD>();
+  const int nb = (r + 7) / 8;
+  const int npairs = nb * (nb + 1) / 2;
+  const bool mine = h < npairs;
+  int kb = 0, rem = mine ? h : 0;
+  while (rem >= nb - kb) { rem -= nb - kb; ++kb; }
+  const int lb = kb + rem;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  bool first = true;
+  RowStage<RPAD, NH> st;
+  if (q0 < q1) st.load(Q, layout, ldq_g, r, q0, (int)min((int64_t)kQsRows, q1 - q0), h);
+  int in_window = 0;
+  for (int64_t s0 = q0; s0 < q1; s0 += kQsRows) {
+    helper_sync<NH>();          // previous rows consumed
+    st.store(Qs, layout, h);
+    helper_sync<NH>();
+    const int64_t s1 = s0 + kQsRows;
+    if (s1 < q1) st.load(Q, layout, ldq_g, r, s1, (int)min((int64_t)kQsRows, q1 - s1), h);
+    if (mine) {
+#pragma unroll 2
+      for (int m = 0; m < kQsRows; ++m) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&Qs[m * LQ + kb * 8]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&Qs[m * LQ + kb * 8 + 4]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&Qs[m * LQ + lb * 8]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&Qs[m * LQ + lb * 8 + 4]);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      }
+    }
+    in_window += kQsRows;
+    if (in_window == 128 || s1 >= q1) {   // fold the window into float64
+      if (mine) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int k = kb * 8 + i, l = lb * 8 + j;
+            if (k < r && l < r) {
+              double* g = gpart + k * r + l;
+              *g = first ? (double)acc[i][j] : *g + (double)acc[i][j];
+            }
+            acc[i][j] = 0.f;
+          }
+      }
+      first = false;
+      in_window = 0;
+    }
+  }
+  if (mine) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int k = kb * 8 + i, l = lb * 8 + j;
+        if (k < r && l < r) {
+          if (first) gpart[k * r + l] = 0.0;           // no rows in this share
+          if (kb != lb) gpart[l * r + k] = gpart[k * r + l];
+        }
+      }
+  }
+  helper_sync<NH>();            // Qs free
+}
+
+template <int RPAD, int NH = kHelpers>
+__device__ void gram_rows(float* Qs, const float* Q, int layout, int64_t ldq_g, int64_t q0,
+                          int64_t q1, int r, double* gpart, int h) {
+  const int nb = (r + 7) / 8;
+  if (RPAD > 64 && nb * (nb + 1) / 2 <= NH)
+    gram_rows8<RPAD, NH>(Qs, Q, layout, ldq_g, q0, q1, r, gpart, h);
+  else
+    gram_rows4<RPAD, NH>(Qs, Q, layout, ldq_g, q0, q1, r, gpart, h);
 }
 
 // Float64 sum, in a fixed order, of the `nparts` partials of entries
@@ -333,13 +465,16 @@ __device__ void finish(float* Ns, const float* Os, const DenTile<RPAD, NH>& den,
       for (int i = 0; i < 4; ++i) {
         const int m = mg + (4 * a + i) * MG;
         if (m >= rows) continue;
-        float v[8];
+        float v[8], o[8], nu[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const int k = kg * 8 + j;
-          const float d = __fadd_rn(den.d[a][i][j], e.eps);
-          v[j] = k < r ? __fdiv_rn(__fmul_rn(Os[m * LO + k], Ns[m * LN + k]), d) : 0.f;
+          o[j] = Os[m * LO + kg * 8 + j];
+          nu[j] = Ns[m * LN + kg * 8 + j];
         }
+        update8(o, nu, den.d[a][i], e.eps, v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (kg * 8 + j >= r) v[j] = 0.f;
 #pragma unroll
         for (int j = 0; j < 8; j += 4)
           *reinterpret_cast<float4*>(&Ns[m * LN + kg * 8 + j]) =
@@ -350,6 +485,107 @@ __device__ void finish(float* Ns, const float* Os, const DenTile<RPAD, NH>& den,
             if (kg * 8 + j < r) e.F[(row0 + m) * r + kg * 8 + j] = v[j];
         }
       }
+  }
+  __syncthreads();
+  for (int i = tid; i < rows * r; i += NT) {
+    const int k = i / rows, m = i % rows;
+    const float v = Ns[m * LN + k];
+    if (e.layout != kFactorRowMajor) e.F[(int64_t)k * e.ldf + row0 + m] = v;
+    store_plane(e, k, row0 + m, v);
+  }
+  (void)R;
+}
+
+// compute_den for DenTile8 (ranks above 64).
+template <int RPAD, int NH = kHelpers>
+__device__ void compute_den(float* Qs, const float* Os, DenTile8<RPAD, NH>& den,
+                            const float* Gpad, int r, int R, int h) {
+  constexpr int LQ = ldq<RPAD>();
+  constexpr int LO = ldo<RPAD>();
+  constexpr int NG = kQsRows * RPAD;
+  constexpr int GV = (NG + NH - 1) / NH;
+  constexpr int KG = DenTile8<RPAD, NH>::KG;
+  constexpr int MG = DenTile8<RPAD, NH>::MG;
+  const int kg = h % KG, mg = h / KG;
+  const bool active = h < KG * MG && mg * 8 < R;
+  auto& acc = den.d;
+  den.clear();
+  int mrow[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) mrow[i] = min(mg * 8 + i, R - 1);
+  float gv[GV];
+  auto gload = [&](int l0) {
+#pragma unroll
+    for (int j = 0; j < GV; ++j) {
+      const int i = h + j * NH;
+      gv[j] = (i < NG && l0 + i / RPAD < r) ? __ldcg(Gpad + l0 * RPAD + i) : 0.f;
+    }
+  };
+  gload(0);
+  for (int l0 = 0; l0 < r; l0 += kQsRows) {
+    helper_sync<NH>();   // previous G rows consumed (and Os complete on entry)
+#pragma unroll
+    for (int j = 0; j < GV; ++j) {
+      const int i = h + j * NH;
+      if (i < NG) Qs[(i / RPAD) * LQ + (i % RPAD)] = gv[j];
+    }
+    helper_sync<NH>();
+    if (l0 + kQsRows < r) gload(l0 + kQsRows);
+    const int nl = min(kQsRows, r - l0);
+    if (active) {
+#pragma unroll 2
+      for (int l = 0; l < nl; ++l) {
+        const float4 g0 = *reinterpret_cast<const float4*>(&Qs[l * LQ + kg * 8]);
+        const float4 g1 = *reinterpret_cast<const float4*>(&Qs[l * LQ + kg * 8 + 4]);
+        const float gw[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float o = Os[mrow[i] * LO + l0 + l];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(o, gw[j], acc[i][j]);
+        }
+      }
+    }
+  }
+}
+
+// finish for DenTile8: as finish(), pass 1 over the helper's 8 x 8 block.
+template <int RPAD, int NT, int HBASE = kHelperBase, int NH = kHelpers>
+__device__ void finish(float* Ns, const float* Os, const DenTile8<RPAD, NH>& den,
+                       const EpiArgs& e, int R, int64_t row0, int rows) {
+  constexpr int LN = epi_ldn<RPAD>();
+  constexpr int LO = ldo<RPAD>();
+  constexpr int KG = DenTile8<RPAD, NH>::KG;
+  constexpr int MG = DenTile8<RPAD, NH>::MG;
+  const int r = e.r;
+  const int tid = threadIdx.x;
+  const int h = tid - HBASE;
+  if (h >= 0 && h < KG * MG) {
+    const int kg = h % KG, mg = h / KG;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int m = mg * 8 + i;
+      if (m >= rows) continue;
+      float v[8], o[8], nu[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        o[j] = Os[m * LO + kg * 8 + j];
+        nu[j] = Ns[m * LN + kg * 8 + j];
+      }
+      update8(o, nu, den.d[i], e.eps, v);
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (kg * 8 + j >= r) v[j] = 0.f;
+#pragma unroll
+      for (int j = 0; j < 8; j += 4)
+        *reinterpret_cast<float4*>(&Ns[m * LN + kg * 8 + j]) =
+            make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+      if (e.layout == kFactorRowMajor) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (kg * 8 + j < r) e.F[(row0 + m) * r + kg * 8 + j] = v[j];
+      }
+    }
   }
   __syncthreads();
   for (int i = tid; i < rows * r; i += NT) {
@@ -449,7 +685,7 @@ __device__ void finish_smem(float* Ns, const float* Os, const float* Ds, const E
     for (int i = tid; i < rows * r; i += NT) {
       const int m = i / r, k = i % r;
       const float d = __fadd_rn(Ds[m * LD + k], e.eps);
-      const float v = __fdiv_rn(__fmul_rn(Os[m * LO + k], Ns[m * LN + k]), d);
+      const float v = div_rn(__fmul_rn(Os[m * LO + k], Ns[m * LN + k]), d);
       e.F[(row0 + m) * r + k] = v;
       Ns[m * LN + k] = v;
     }
@@ -462,7 +698,7 @@ __device__ void finish_smem(float* Ns, const float* Os, const float* Ds, const E
     for (int i = tid; i < rows * r; i += NT) {
       const int k = i / rows, m = i % rows;
       const float d = __fadd_rn(Ds[m * LD + k], e.eps);
-      const float v = __fdiv_rn(__fmul_rn(Os[m * LO + k], Ns[m * LN + k]), d);
+      const float v = div_rn(__fmul_rn(Os[m * LO + k], Ns[m * LN + k]), d);
       e.F[(int64_t)k * e.ldf + row0 + m] = v;
       store_plane(e, k, row0 + m, v);
     }

@@ -124,6 +124,16 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   d |= (uint64_t)2 << 61;                      // layout: 128-byte swizzle
   return d;
 }
+// Same for 64-byte rows (64-byte swizzle, atoms of 8 rows x 64 B).
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address, bits 0-13
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused here)
+  d |= (uint64_t)(512 >> 4) << 32;             // stride byte offset: 8 rows x 64 B
+  d |= (uint64_t)1 << 46;                      // descriptor version (tcgen05)
+  d |= (uint64_t)4 << 61;                      // layout: 64-byte swizzle
+  return d;
+}
 // Instruction descriptor: D f32, A/B of `fmt` (1 = bf16 under kind::f16,
 // 2 = tf32 under kind::tf32), both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc(uint32_t fmt, int M, int N) {

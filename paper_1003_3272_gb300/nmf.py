@@ -45,6 +45,7 @@ EXPORTS = [
     "nmf_batched_step", "nmf_batched_objective", "nmf_batched_destroy",
     "nmf_status_str", "nmf_last_error", "nmf_version", "nmf_restart",
     "nmf_kernel_launches", "nmf_profile_enable", "nmf_profile_read", "nmf_gram_noalloc",
+    "nmf_selfcheck_div",
 ]
 
 _lib = None
@@ -85,6 +86,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "nmf_restart": ([c_p, ctypes.c_uint64], ctypes.c_int),
         "nmf_kernel_launches": ([], ctypes.c_uint64),
         "nmf_gram_noalloc": ([c_p, i32, i64, i64, i32, c_p, c_p], ctypes.c_int),
+        "nmf_selfcheck_div": ([i64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
+                               ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
         "nmf_profile_enable": ([c_p, ctypes.c_int], ctypes.c_int),
         "nmf_profile_read": ([c_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -100,6 +103,15 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
 def kernel_launches() -> int:
     """Kernels launched by the library so far in this process."""
     return int(load().nmf_kernel_launches())
+
+
+def selfcheck_div(count: int, seed: int = 1):
+    """(mismatches, quick) of the update's division against the IEEE
+    division over `count` operand pairs on the current device."""
+    lib = load()
+    mm, q = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib.nmf_selfcheck_div(count, seed, ctypes.byref(mm), ctypes.byref(q)))
+    return mm.value, q.value
 
 
 class NMFError(RuntimeError):

@@ -227,3 +227,15 @@ def test_planted_full_size_sampled():
         GH = H1 @ H1.T
         Ws = W0[rows] * (V64[rows] @ H1.T) / (W0[rows] @ GH + pr.eps)
         assert entry_rel_err(W1[rows], Ws)[0] < 5e-5
+
+
+def test_update_division_is_the_ieee_division():
+    """The update divides by Markstein's quotient correction where its
+    conditions hold: every significand of the divisor against 64 dividends,
+    plus random operand pairs over the whole float32 range, bit for bit
+    against the IEEE division."""
+    from paper_1003_3272_gb300 import nmf
+    count = (64 << 23) + (1 << 29)
+    mism, quick = nmf.selfcheck_div(count, seed=7)
+    assert mism == 0
+    assert quick > (64 << 23)          # the sweep and most random pairs took the quick form
