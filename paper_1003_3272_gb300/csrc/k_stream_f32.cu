@@ -290,6 +290,7 @@ k_stream_f32(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUt
     }
     cluster.sync();   // every block's partial tile is in its shared memory
     if (!abort) {
+      // rows [q R, (q+1) R) of the tile: the S partial tiles summed in rank order
       for (int i = threadIdx.x; i < R * (RPAD / 4); i += kThreads) {
         const int m = i / (RPAD / 4), k4 = (i % (RPAD / 4)) * 4;
         const float4* mine = reinterpret_cast<const float4*>(&Acc[(q * R + m) * LDA + k4]);

@@ -409,20 +409,8 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
     // of a cluster, aborted or not, so no block can wait on a peer forever.
     cluster.sync();   // every block's partial tile is in its shared memory
     if (!abort) {
-      // rows [q R, (q+1) R) of the tile: sum the S partial tiles in rank order
-      for (int i = threadIdx.x; i < R * (RPAD / 4); i += kThreads) {
-        const int m = i / (RPAD / 4), k4 = (i % (RPAD / 4)) * 4;
-        const float4* mine = reinterpret_cast<const float4*>(&Acc[(q * R + m) * LDA + k4]);
-        float4 v[8];
-#pragma unroll
-        for (int s = 0; s < 8; ++s)
-          if (s < S) v[s] = *cluster.map_shared_rank(mine, s);   // all loads first
-        float4 sum = v[0];
-#pragma unroll
-        for (int s = 1; s < 8; ++s)
-          if (s < S) { sum.x += v[s].x; sum.y += v[s].y; sum.z += v[s].z; sum.w += v[s].w; }
-        *reinterpret_cast<float4*>(&Ns[m * LDN + k4]) = sum;
-      }
+      // rows [q R, (q+1) R) of the tile: the S partial tiles summed in rank order
+      tcepi::cluster_sum<RPAD, kThreads>(S, Acc, Ns, q);
     }
     cluster.sync();   // peers are done reading this block's tile
     if (!*(volatile int*)&s_abort) tcepi::finish<RPAD, kThreads>(Ns, Os, den, a.ep, R, row0, rows);

@@ -17,6 +17,8 @@
 // and writes the factor and its operand plane(s).
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include <type_traits>
 
 #include "epilogue.cuh"
@@ -82,12 +84,13 @@ using DenFor = typename std::conditional<(RPAD > 64), DenTile8<RPAD, NH>, DenTil
 // new = (old * num) / (den + eps) for 8 entries at once: the quick
 // correctly rounded divisions first (independent, so they overlap), then the
 // IEEE division for any entry outside the quick form's range.
+template <int N = 8>
 __device__ __forceinline__ void update8(const float* old, const float* num, const float* den,
                                         float eps, float* v) {
-  float x[8], d[8];
+  float x[N], d[N];
   bool slow = false;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
+  for (int j = 0; j < N; ++j) {
     x[j] = __fmul_rn(old[j], num[j]);
     d[j] = __fadd_rn(den[j], eps);
     slow |= !div_rn_quick_ok(x[j], d[j]);
@@ -95,7 +98,7 @@ __device__ __forceinline__ void update8(const float* old, const float* num, cons
   }
   if (slow) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
+    for (int j = 0; j < N; ++j)
       if (!div_rn_quick_ok(x[j], d[j])) v[j] = __fdiv_rn(x[j], d[j]);
   }
 }
@@ -103,6 +106,72 @@ __device__ __forceinline__ void update8(const float* old, const float* num, cons
 template <int NH = kHelpers>
 __device__ __forceinline__ void helper_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(NH) : "memory");
+}
+
+// Sum, in rank order, of the S partial tiles of a cluster (each block's
+// Acc[128][LDA] in its shared memory) over this block's rows [q R, (q+1) R),
+// R = 128 / S, into Ns[R][LN]: every thread issues all of its distributed
+// shared-memory loads before it adds, so the cluster's round trips overlap.
+template <int S, int RPAD, int NT>
+__device__ void cluster_sum_s(const float* Acc, float* Ns, int q) {
+  constexpr int R = 128 / S;
+  constexpr int NQ = RPAD / 4;
+  constexpr int TOT = R * NQ;
+  constexpr int J = (TOT + NT - 1) / NT;
+  constexpr int JC = (8 / S) < 1 ? 1 : (8 / S);   // at most 8 loads in flight
+  constexpr int LDA = RPAD + 4;
+  constexpr int LN = epi_ldn<RPAD>();
+  cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
+#pragma unroll 1
+  for (int j0 = 0; j0 < J; j0 += JC) {
+    float4 v[JC][S];
+#pragma unroll
+    for (int j = 0; j < JC; ++j) {
+      const int i = threadIdx.x + (j0 + j) * NT;
+      if (j0 + j < J && i < TOT) {
+        const int m = i / NQ, k4 = (i - m * NQ) * 4;
+        const float4* mine = reinterpret_cast<const float4*>(&Acc[(q * R + m) * LDA + k4]);
+#pragma unroll
+        for (int s = 0; s < S; ++s) v[j][s] = *cluster.map_shared_rank(mine, s);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < JC; ++j) {
+      const int i = threadIdx.x + (j0 + j) * NT;
+      if (j0 + j < J && i < TOT) {
+        const int m = i / NQ, k4 = (i - m * NQ) * 4;
+        float4 sum = v[j][0];
+#pragma unroll
+        for (int s = 1; s < S; ++s) {
+          sum.x += v[j][s].x; sum.y += v[j][s].y; sum.z += v[j][s].z; sum.w += v[j][s].w;
+        }
+        *reinterpret_cast<float4*>(&Ns[m * LN + k4]) = sum;
+      }
+    }
+  }
+}
+
+template <int RPAD, int NT>
+__device__ void cluster_sum(int S, const float* Acc, float* Ns, int q) {
+  if (S == 2) cluster_sum_s<2, RPAD, NT>(Acc, Ns, q);
+  else if (S == 4) cluster_sum_s<4, RPAD, NT>(Acc, Ns, q);
+  else cluster_sum_s<8, RPAD, NT>(Acc, Ns, q);
+}
+
+// Pass 2 of an update: the [k][m]-ordered outputs (planes, and H itself) of
+// the slice's new values Ns[m][k], 8 consecutive rows per thread and step.
+template <int RPAD, int NT>
+__device__ void store_cols(const float* Ns, const EpiArgs& e, int64_t row0, int rows) {
+  constexpr int LN = epi_ldn<RPAD>();
+  const int ng = (rows + 7) >> 3;
+  for (int i = threadIdx.x; i < e.r * ng; i += NT) {
+    const int k = i / ng, m0 = (i - k * ng) * 8;
+    const int n8 = min(8, rows - m0);
+    float v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = t < n8 ? Ns[(m0 + t) * LN + k] : 0.f;
+    store_col8(e, k, row0 + m0, n8, v);
+  }
 }
 
 // Values of rows [m0, m0 + nrows) (nrows <= kQsRows) of a factor, in the
@@ -487,12 +556,7 @@ __device__ void finish(float* Ns, const float* Os, const DenTile<RPAD, NH>& den,
       }
   }
   __syncthreads();
-  for (int i = tid; i < rows * r; i += NT) {
-    const int k = i / rows, m = i % rows;
-    const float v = Ns[m * LN + k];
-    if (e.layout != kFactorRowMajor) e.F[(int64_t)k * e.ldf + row0 + m] = v;
-    store_plane(e, k, row0 + m, v);
-  }
+  store_cols<RPAD, NT>(Ns, e, row0, rows);
   (void)R;
 }
 
@@ -588,12 +652,7 @@ __device__ void finish(float* Ns, const float* Os, const DenTile8<RPAD, NH>& den
     }
   }
   __syncthreads();
-  for (int i = tid; i < rows * r; i += NT) {
-    const int k = i / rows, m = i % rows;
-    const float v = Ns[m * LN + k];
-    if (e.layout != kFactorRowMajor) e.F[(int64_t)k * e.ldf + row0 + m] = v;
-    store_plane(e, k, row0 + m, v);
-  }
+  store_cols<RPAD, NT>(Ns, e, row0, rows);
   (void)R;
 }
 
@@ -672,37 +731,39 @@ __device__ void compute_den_smem(float* Qs, const float* Os, float* Ds, const fl
 }
 
 // finish() with the denominators in Ds: every thread of the block takes part
-// in both passes.
+// in both passes; pass 1 works on 8 consecutive ranks of a row at a time.
 template <int RPAD, int NT>
 __device__ void finish_smem(float* Ns, const float* Os, const float* Ds, const EpiArgs& e,
                             int R, int64_t row0, int rows) {
   constexpr int LN = epi_ldn<RPAD>();
   constexpr int LO = ldo<RPAD>();
   constexpr int LD = ldd<RPAD>();
+  constexpr int KG = RPAD / 4;
   const int r = e.r;
-  const int tid = threadIdx.x;
-  if (e.layout == kFactorRowMajor) {
-    for (int i = tid; i < rows * r; i += NT) {
-      const int m = i / r, k = i % r;
-      const float d = __fadd_rn(Ds[m * LD + k], e.eps);
-      const float v = div_rn(__fmul_rn(Os[m * LO + k], Ns[m * LN + k]), d);
-      e.F[(row0 + m) * r + k] = v;
-      Ns[m * LN + k] = v;
+  for (int i = threadIdx.x; i < rows * KG; i += NT) {
+    const int m = i / KG, k0 = (i - m * KG) * 4;
+    if (k0 >= r) continue;
+    float o[4], nu[4], v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      o[j] = Os[m * LO + k0 + j];
+      nu[j] = Ns[m * LN + k0 + j];
     }
-    __syncthreads();
-    for (int i = tid; i < rows * r; i += NT) {
-      const int k = i / rows, m = i % rows;
-      store_plane(e, k, row0 + m, Ns[m * LN + k]);
-    }
-  } else {
-    for (int i = tid; i < rows * r; i += NT) {
-      const int k = i / rows, m = i % rows;
-      const float d = __fadd_rn(Ds[m * LD + k], e.eps);
-      const float v = div_rn(__fmul_rn(Os[m * LO + k], Ns[m * LN + k]), d);
-      e.F[(int64_t)k * e.ldf + row0 + m] = v;
-      store_plane(e, k, row0 + m, v);
+    const float4 dn = *reinterpret_cast<const float4*>(&Ds[m * LD + k0]);
+    const float dv[4] = {dn.x, dn.y, dn.z, dn.w};
+    update8<4>(o, nu, dv, e.eps, v);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (k0 + j >= r) v[j] = 0.f;
+    *reinterpret_cast<float4*>(&Ns[m * LN + k0]) = make_float4(v[0], v[1], v[2], v[3]);
+    if (e.layout == kFactorRowMajor) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (k0 + j < r) e.F[(row0 + m) * r + k0 + j] = v[j];
     }
   }
+  __syncthreads();
+  store_cols<RPAD, NT>(Ns, e, row0, rows);
   (void)R;
 }
 
