@@ -128,15 +128,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, backend=None):
+    """One process per GPU (torchrun's RANK / LOCAL_RANK / WORLD_SIZE); NCCL
+    on GPUs, gloo where there is none (the host-side logic's tests)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     return ws, rank, local
 
 
@@ -151,9 +156,16 @@ def max_over_ranks(x, ws):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(units_per_rank, seconds, ws):
+    """Whole-job throughput of `ws` replicas: the units all ranks processed
+    over the slowest rank's time (the time is already the max over ranks)."""
+    return units_per_rank * ws / seconds
 
 
 def algorithmic(prec, p, n, r):
@@ -265,7 +277,7 @@ def time_planted(pr, prec, steps, warmup, ws, local, sample_clocks=False, profil
     ms = max_over_ranks(e0.elapsed_time(e1), ws)
     res = {"prec": prec, "ms": ms, "steps": steps, "launches": int(launches),
            "clocks": clocks, "objective": fs[-1],
-           "value": iters * steps * ws / (ms / 1e3)}
+           "value": job_rate(iters * steps, ms / 1e3, ws)}
     if profile:
         res["kinds"] = {k: ctx.profile_read(i) for i, k in
                         enumerate(["stream_products", "gram_reductions", "objective", "restart"])}

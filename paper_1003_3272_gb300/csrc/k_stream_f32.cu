@@ -10,8 +10,10 @@
 // shared memory and the helper warps (tc_epi.cuh), which formed the other
 // factor's Gram and the denominators during the stream, finish the update.
 // The difference: the product is accumulated with float32 FMAs on the SM
-// cores by eight compute warps (thread tile 4 rows x TR ranks, RPAD = 8 TR),
-// reading the swizzled stages with bank-conflict-free 16-byte loads.
+// cores by eight compute warps (thread tile 4 rows x TR ranks, RPAD = 8 TR;
+// for TR <= 4, 8 rows in two groups that split each stage's K, their partial
+// tiles added in a fixed order), reading the swizzled stages with
+// bank-conflict-free 16-byte loads.
 //
 // Warps: 0 = TMA producer (one lane); 1-8 = compute; 9-11 = helpers.
 #include <cooperative_groups.h>
@@ -171,10 +173,20 @@ k_stream_f32(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUt
     tcepi::helper_sync<kNH>();
   }
 
-  // compute thread layout: rows rg + 32 i (i < 4), ranks cg + 8 t (t < TR)
+  // compute thread layout: RT rows x TR ranks per thread.  RT = 8 (TR <= 4):
+  // two groups of four warps split each stage's K (16-byte chunks 0-3 and
+  // 4-7), rows rg + 16 i; RT = 4: one group, rows rg + 32 i.  Ranks cgi + 8 t.
+  // (The 8-row tile halves the X loads per FMA; above TR = 4 its registers
+  // cost more than that saves.)
+  constexpr int RT = TR <= 4 ? 8 : 4;
+  constexpr int NKG = RT / 4;                 // K groups
+  constexpr int TPG = 256 / NKG;              // threads per group
+  constexpr int RS = 128 / RT;                // row stride
+  constexpr int CPG = 8 / NKG;                // 16-byte K chunks per group and stage
   const int c = threadIdx.x - kCompute0;
-  const int rg = ((c >> 5) << 2) + (c & 3);   // 0..31
-  const int cgi = (c & 31) >> 2;              // 0..7
+  const int kgrp = NKG == 2 ? ((c >> 7) & 1) : 0;
+  const int rg = (((c % TPG) >> 5) << 2) + (c & 3);   // 0 .. RS-1
+  const int cgi = (c & 31) >> 2;                      // 0..7
 
   int it = 0;
   int kb_base = 0;
@@ -183,9 +195,9 @@ k_stream_f32(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUt
     const int64_t row0 = m0 + (int64_t)q * R;
     const int rows = (int)max((int64_t)0, min((int64_t)R, a.M - row0));
     const int nkb_run = *(volatile int*)&s_abort ? 0 : nkb;
-    float acc[4][TR];
+    float acc[RT][TR];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RT; ++i)
 #pragma unroll
       for (int t = 0; t < TR; ++t) acc[i][t] = 0.f;
 
@@ -247,18 +259,19 @@ k_stream_f32(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUt
         const uint8_t* xb = smem + s * Sh::STAGE + rg * 128;
         const uint8_t* yb = smem + s * Sh::STAGE + Sh::X_BYTES + cgi * 128;
 #pragma unroll
-        for (int c4 = 0; c4 < 8; ++c4) {
+        for (int cc = 0; cc < CPG; ++cc) {
+          const int c4 = kgrp * CPG + cc;
           const int xo = (c4 ^ (rg & 7)) << 4;
           const int yo = (c4 ^ cgi) << 4;
-          float4 xv[4], yv[TR];
+          float4 xv[RT], yv[TR];
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
-            xv[i] = *reinterpret_cast<const float4*>(xb + i * (32 * 128) + xo);
+          for (int i = 0; i < RT; ++i)
+            xv[i] = *reinterpret_cast<const float4*>(xb + i * (RS * 128) + xo);
 #pragma unroll
           for (int t = 0; t < TR; ++t)
             yv[t] = *reinterpret_cast<const float4*>(yb + t * (8 * 128) + yo);
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < RT; ++i)
 #pragma unroll
             for (int t = 0; t < TR; ++t) {
               acc[i][t] = fmaf(xv[i].x, yv[t].x, acc[i][t]);
@@ -282,11 +295,24 @@ k_stream_f32(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUt
 
     float* Acc = reinterpret_cast<float*>(smem);
     float* Ns = reinterpret_cast<float*>(smem + Sh::ACC);
-    if (compute && !abort) {
+    // the K groups' partial sums: group 1 stores, group 0 adds (fixed order)
+    if (compute && !abort && kgrp == NKG - 1) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RT; ++i)
 #pragma unroll
-        for (int t = 0; t < TR; ++t) Acc[(rg + 32 * i) * LDA + cgi + 8 * t] = acc[i][t];
+        for (int t = 0; t < TR; ++t) Acc[(rg + RS * i) * LDA + cgi + 8 * t] = acc[i][t];
+    }
+    if (NKG == 2) {
+      if (compute) asm volatile("bar.sync 2, 256;" ::: "memory");   // the compute warps
+      if (compute && !abort && kgrp == 0) {
+#pragma unroll
+        for (int i = 0; i < RT; ++i)
+#pragma unroll
+          for (int t = 0; t < TR; ++t) {
+            float* p = &Acc[(rg + RS * i) * LDA + cgi + 8 * t];
+            *p = acc[i][t] + *p;
+          }
+      }
     }
     cluster.sync();   // every block's partial tile is in its shared memory
     if (!abort) {
