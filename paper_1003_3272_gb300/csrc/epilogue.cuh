@@ -16,17 +16,9 @@
 
 namespace nmf {
 
-// Row strides of the epilogue's shared tiles: Ns (numerator, then new
-// factor) keeps 16-byte aligned rows for the Gram's vector loads; Os (old
-// factor) uses an odd stride so that column reads are bank-conflict free.
+// Row stride of the epilogue's shared tile Ns (numerator, then new factor):
+// 16-byte aligned rows for vector access.
 template <int RPAD> __host__ __device__ constexpr int epi_ldn() { return RPAD + 4; }
-template <int RPAD> __host__ __device__ constexpr int epi_ldo() { return RPAD + 1; }
-
-// Shared-memory floats needed by mu_epilogue for an R x RPAD slice.
-template <int RPAD>
-__host__ __device__ constexpr int epi_smem_floats(int R) {
-  return R * epi_ldn<RPAD>() + R * epi_ldo<RPAD>() + RPAD * RPAD;
-}
 
 __device__ __forceinline__ void store_plane(const EpiArgs& e, int k, int64_t m, float v) {
   const int64_t off = (int64_t)k * e.ldop + m;

@@ -332,10 +332,10 @@ nmf_status build_ctx(nmf_ctx* c) {
 
   hh.ep.F = c->H; hh.ep.ldf = n; hh.ep.layout = kFactorColMajor; hh.ep.M = n;
   hh.ep.op_hi = c->Hop_hi; hh.ep.op_lo = c->Hop_lo; hh.ep.ldop = c->ld_n;
-  hh.ep.G = c->GW32; hh.G32_out = c->GH32; hh.G64_out = c->GH64; hh.own = 1;
+  hh.G32_out = c->GH32; hh.G64_out = c->GH64; hh.own = 1;
   hw.ep.F = c->W; hw.ep.ldf = r; hw.ep.layout = kFactorRowMajor; hw.ep.M = p;
   hw.ep.op_hi = c->Wop_hi; hw.ep.op_lo = c->Wop_lo; hw.ep.ldop = c->ld_p;
-  hw.ep.G = c->GH32; hw.G32_out = c->GW32; hw.G64_out = c->GW64; hw.own = 0;
+  hw.G32_out = c->GW32; hw.G64_out = c->GW64; hw.own = 0;
 
   const size_t gtiles[2] = {(size_t)ceil_div(p, 128), (size_t)ceil_div(n, 128)};
   for (HalfPlan* h : {&hh, &hw}) {
@@ -361,7 +361,6 @@ nmf_status build_ctx(nmf_ctx* c) {
     const size_t grid = (size_t)(hh.tc.grid > hw.tc.grid ? hh.tc.grid : hw.tc.grid);
     if ((s = dalloc(c, (void**)&c->tc_gpart, grid * rr * 8)) != NMF_OK) return s;
   }
-  for (HalfPlan* h : {&hh, &hw}) h->ep.gram_part = c->gpart[h->own];
   if ((s = dalloc(c, (void**)&c->obj_parts, objective_parts() * 8)) != NMF_OK) return s;
   if ((s = dalloc(c, (void**)&c->f_dev, 8)) != NMF_OK) return s;
   if ((s = dalloc(c, (void**)&c->err_dev, sizeof(int))) != NMF_OK) return s;
