@@ -2,10 +2,15 @@
 // problems (Section 3.1, Eqs. (3.3)-(3.4)) updated together.
 //
 // Per half step of every instance b (H update, then W update):
-//   k_batched_gram : the r_b x r_b Gram of the factor that is *not* updated,
-//                    one block per 256-row chunk of each instance (float32
-//                    within 128-row windows, float64 across them, summed in
-//                    chunk order by the instance's last block).
+//   k_batched_tc   : (below) also leaves, per item, the float32 Gram of the
+//                    item's 128 new factor rows, in float64, for the next
+//                    half step;
+//   k_batched_gram_reduce : sums each instance's item Grams in tile order
+//                    (float64) into the Gram the next half step divides by.
+//   k_batched_gram : the same Gram from scratch (start and restarts), one
+//                    block per 256-row chunk of each instance (float32 within
+//                    128-row windows, float64 across them, summed in chunk
+//                    order by the instance's last block).
 //   k_batched_tc   : a persistent grid walks a host-scheduled list of
 //                    (instance, 128-row tile) items; per item the whole K
 //                    range of the tile is streamed (TMA, tile-blocked V
@@ -51,6 +56,7 @@ struct BatchInst {
   void* op_lo[2];
   int64_t ldop[2];
   const float* Gpad[2];       // [half]: Gram of the other factor, kBR x kBR fp32 (padded)
+  int slot0[2];               // [half]: first item-Gram slot of this instance's tiles
   int nkbt[2];                // k-blocks per tile row of X
   int tmap;                   // first of eight maps: [half][x_hi, x_lo, y_hi, y_lo]
   int plane;                  // PlaneKind
@@ -63,6 +69,7 @@ struct BatchParams {
   const int* cta_off;         // items of block c: [cta_off[c], cta_off[c + 1])
   int half;
   int* err;
+  double* gitem;              // [slot][kBR * kBR] Grams of the items' new rows
 };
 
 template <int PREC>
@@ -78,12 +85,24 @@ struct BShape {
   static constexpr int Y_BYTES = kBR * 128;
   static constexpr int STAGE = XPL * (X_BYTES + Y_BYTES);
   static constexpr int GS = kBR * kBR * 4;                 // the instance's Gram
-  static constexpr int STAGES_RAW = (kSmemMax - GS - 2048) / STAGE;
+  static constexpr int VLD = kBR + 4;                      // new rows, 16-byte aligned
+  static constexpr int VS = kBM * VLD * 4;
+  static constexpr int STAGES_RAW = (kSmemMax - GS - VS - 2048) / STAGE;
   static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
-  static constexpr int SMEM = STAGES * STAGE + GS + 1024;
+  static constexpr int SMEM = STAGES * STAGE + GS + VS + 1024;
 };
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// epi_sync that also returns, to every epilogue thread alike, whether any of
+// them passed `flag` true (so that all of them leave a loop together).
+__device__ __forceinline__ bool epi_sync_or(bool flag) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r) : "r"((uint32_t)flag) : "memory");
+  return r != 0;
+}
 
 __device__ __forceinline__ void plane_store(int plane, void* hi, void* lo, int64_t off, float v) {
   if (plane == kPlaneTF32) {
@@ -117,6 +136,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(const BatchParams a)
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = ptx::smem_u32(smem);
   float* Gs = reinterpret_cast<float*>(smem + STAGES * Sh::STAGE);
+  float* Vs = reinterpret_cast<float*>(smem + STAGES * Sh::STAGE + Sh::GS);   // [kBM][VLD]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int half = a.half;
   const int i0 = a.cta_off[blockIdx.x], i1 = a.cta_off[blockIdx.x + 1];
@@ -150,8 +170,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(const BatchParams a)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer: every k-block of every item ----------
-    ptx::pdl_wait();
-    ptx::pdl_launch_dependents();
+    // The Gram launch before this one (the programmatic predecessor) writes
+    // only the Grams, which the epilogue waits for; V's copies and the factor
+    // planes were final before that launch began, so streaming starts at once.
     int g = 0;
     for (int i = i0; i < i1 && !*(volatile int*)&s_abort; ++i) {
       const int2 it = a.items[i];
@@ -233,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(const BatchParams a)
     const int et = threadIdx.x - 64;
     const int quarter = warp & 3;                 // TMEM lanes 32 * (warp % 4)
     const int row = quarter * 32 + lane;
-    ptx::pdl_wait();                              // the factors of the previous launch are final
+    ptx::pdl_wait();                              // the Gram launch has completed
     for (int i = i0; i < i1; ++i) {
       const int buf = (i - i0) & 1;
       const uint32_t use = (uint32_t)((i - i0) >> 1);
@@ -262,10 +283,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(const BatchParams a)
       }
       ptx::tc_fence_before();
       ptx::mbar_arrive(ptx::smem_u32(&acce[buf]));
-      epi_sync();   // Gs complete; an expired wait is visible to all epilogue threads
-      if (*(volatile int*)&s_abort) break;
+      // Gs complete; an expired wait anywhere stops every epilogue thread alike
+      if (epi_sync_or(*(volatile int*)&s_abort != 0)) break;
       const int64_t M = B.M[half];
       const int64_t m = (int64_t)it.y * kBM + row;
+      float* vrow = Vs + row * Sh::VLD;
+#pragma unroll
+      for (int k = 0; k < kBR; k += 4)
+        *reinterpret_cast<float4*>(vrow + k) = make_float4(0.f, 0.f, 0.f, 0.f);
       if (m < M) {
         float old[kBR];
         float* F = B.F[half];
@@ -285,6 +310,50 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(const BatchParams a)
           if (half == 0) F[(int64_t)k * ldf + m] = v;
           else           F[m * ldf + k] = v;
           plane_store(B.plane, B.op_hi[half], B.op_lo[half], (int64_t)k * B.ldop[half] + m, v);
+          vrow[k] = v;
+        }
+      }
+      // Gram of the item's new rows (float32 over its 128 rows): two groups of
+      // 64 threads take 64 rows each, one 4 x 4 block of the 32 x 32 per
+      // thread; group 1's sums go through Gs (free until the next item),
+      // group 0 adds them and stores the float64 result in the item's slot.
+      epi_sync();
+      {
+        const int grp = et >> 6, bi = (et >> 3) & 7, bj = et & 7;
+        float acc[4][4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+        if (bi * 4 < r && bj * 4 < r) {
+#pragma unroll 4
+          for (int mm = 0; mm < 64; ++mm) {
+            const float* vr = Vs + (grp * 64 + mm) * Sh::VLD;
+            const float4 va = *reinterpret_cast<const float4*>(vr + bi * 4);
+            const float4 vb = *reinterpret_cast<const float4*>(vr + bj * 4);
+            const float av[4] = {va.x, va.y, va.z, va.w};
+            const float bv[4] = {vb.x, vb.y, vb.z, vb.w};
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+              for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
+          }
+        }
+        if (grp == 1) {
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) Gs[(et & 63) * 16 + x * 4 + y] = acc[x][y];
+        }
+        epi_sync();
+        if (grp == 0) {
+          double* dst = a.gitem + (int64_t)(B.slot0[half] + it.y) * (kBR * kBR);
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y)
+              dst[(bi * 4 + x) * kBR + bj * 4 + y] =
+                  (double)__fadd_rn(acc[x][y], Gs[et * 16 + x * 4 + y]);
         }
       }
     }
@@ -327,20 +396,38 @@ k_batched_gram(const GramInst* gi, const int2* items, double* gpart) {
   __shared__ __align__(16) float Qs[2][128][kGramLd];
   __shared__ double red[64][16];
   __shared__ int s_last;
+  // The grouped product of this half step may start now: only its epilogue
+  // reads the Grams, after waiting for this grid (griddepcontrol.wait).
+  ptx::pdl_launch_dependents();
   const int2 it = items[blockIdx.x];
   const GramInst g = gi[it.x];
   const int t = threadIdx.x;
   const int64_t row0 = (int64_t)(it.y - g.chunk0) * kGramChunk;
-  // stage 256 rows x kBR (zero beyond r and beyond QM)
-  for (int q = t; q < kGramChunk * kBR; q += kGramThreads) {
-    int m, k;
-    if (g.layout == 1) { k = q / kGramChunk; m = q % kGramChunk; }
-    else               { m = q / kBR; k = q % kBR; }
-    const int64_t row = row0 + m;
-    float v = 0.f;
-    if (k < g.r && row < g.QM)
-      v = g.layout == 1 ? g.Q[(int64_t)k * g.ldq + row] : g.Q[row * g.ldq + k];
-    Qs[m >> 7][m & 127][k] = v;
+  // stage 256 rows x kBR (zero beyond r and beyond QM), 16 loads in flight
+  // per thread
+  constexpr int kPer = kGramChunk * kBR / kGramThreads;   // 64
+#pragma unroll
+  for (int q0 = 0; q0 < kPer; q0 += 16) {
+    float v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int q = t + (q0 + j) * kGramThreads;
+      int m, k;
+      if (g.layout == 1) { k = q / kGramChunk; m = q % kGramChunk; }
+      else               { m = q / kBR; k = q % kBR; }
+      const int64_t row = row0 + m;
+      v[j] = (k < g.r && row < g.QM)
+                 ? __ldg(g.layout == 1 ? g.Q + (int64_t)k * g.ldq + row : g.Q + row * g.ldq + k)
+                 : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int q = t + (q0 + j) * kGramThreads;
+      int m, k;
+      if (g.layout == 1) { k = q / kGramChunk; m = q % kGramChunk; }
+      else               { m = q / kBR; k = q % kBR; }
+      Qs[m >> 7][m & 127][k] = v[j];
+    }
   }
   __syncthreads();
   const int grp = t >> 6, bi = (t & 63) >> 3, bj = t & 7;
@@ -391,8 +478,26 @@ k_batched_gram(const GramInst* gi, const int2* items, double* gpart) {
     }
     if (t == 0) *g.done = 0u;
   }
-  // the next kernel may be scheduled; it waits for this grid before reading
+}
+
+// Gram for the next half step: instance b's item Grams of half `half` (the
+// factor that half updated) summed in tile order in float64, into the padded
+// float32 Gram of the other half.  One block per instance.  Lets the next
+// grouped launch start right away (its epilogue waits for this grid).
+__global__ void __launch_bounds__(256)
+k_batched_gram_reduce(const BatchInst* inst, const double* gitem, int half) {
   ptx::pdl_launch_dependents();
+  const BatchInst& B = inst[blockIdx.x];
+  const int tiles = (int)ceil_div(B.M[half], (int64_t)kBM);
+  const double* src = gitem + (int64_t)B.slot0[half] * (kBR * kBR);
+  float* Gpad = const_cast<float*>(B.Gpad[1 - half]);
+  for (int e = threadIdx.x; e < kBR * kBR; e += 256) {
+    const int k = e / kBR, l = e % kBR;
+    double sum = 0.0;
+    if (k < B.r && l < B.r)
+      for (int t = 0; t < tiles; ++t) sum += __ldcg(src + (int64_t)t * (kBR * kBR) + e);
+    Gpad[e] = (float)sum;
+  }
 }
 
 // Objective of every instance: f_b = ||V_b - W_b H_b||_F^2, tiles of 64 x 128
@@ -562,6 +667,7 @@ struct nmf_batch {
   int gblocks[2] = {0, 0};
   double* d_gpart = nullptr;                 // per-chunk float64 partials
   unsigned int* d_gdone = nullptr;           // [2][count] finished-block counters
+  double* d_gitem = nullptr;                 // item Grams [slot][kBR * kBR]
   ObjInst* d_obj = nullptr;
   int* d_tile_inst = nullptr;
   int obj_tiles = 0;
@@ -632,7 +738,8 @@ cudaError_t launch_batched_tc(nmf_batch* b, int half) {
     if (e != cudaSuccess) return e;
     done = true;
   }
-  BatchParams prm{b->d_inst, b->d_maps, b->d_items[half], b->d_off[half], half, b->d_err};
+  BatchParams prm{b->d_inst, b->d_maps, b->d_items[half], b->d_off[half], half, b->d_err,
+                  b->d_gitem};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)b->grid[half]);
   cfg.blockDim = dim3(kThreads);
@@ -646,19 +753,29 @@ cudaError_t launch_batched_tc(nmf_batch* b, int half) {
   return cudaLaunchKernelEx(&cfg, kern, prm);
 }
 
+// The Gram of W for the first H update, from W itself (at the start and
+// whenever the factors are reset).
+cudaError_t start_gram(nmf_batch* b) {
+  k_batched_gram<<<b->gblocks[0], kGramThreads, 0, b->st>>>(b->d_gram[0], b->d_gitems[0],
+                                                            b->d_gpart);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// One half step: the grouped product and update (which also leaves the item
+// Grams of the new factor), then the Gram the other half divides by.
 cudaError_t launch_half(nmf_batch* b, int half) {
-  // Gram of the other factor: half 0 (H update) needs W^T W, half 1 needs H H^T
-  k_batched_gram<<<b->gblocks[half], kGramThreads, 0, b->st>>>(b->d_gram[half],
-                                                                 b->d_gitems[half], b->d_gpart);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  count_launches(2);
+  cudaError_t e;
   switch (b->prec) {
-    case NMF_TF32: return launch_batched_tc<NMF_TF32>(b, half);
-    case NMF_BF16X3: return launch_batched_tc<NMF_BF16X3>(b, half);
-    case NMF_BF16: return launch_batched_tc<NMF_BF16>(b, half);
+    case NMF_TF32: e = launch_batched_tc<NMF_TF32>(b, half); break;
+    case NMF_BF16X3: e = launch_batched_tc<NMF_BF16X3>(b, half); break;
+    case NMF_BF16: e = launch_batched_tc<NMF_BF16>(b, half); break;
     default: return cudaErrorInvalidValue;
   }
+  if (e != cudaSuccess) return e;
+  k_batched_gram_reduce<<<b->count, 256, 0, b->st>>>(b->d_inst, b->d_gitem, half);
+  count_launches(2);
+  return cudaGetLastError();
 }
 
 cudaError_t run_iteration(nmf_batch* b) {
@@ -816,6 +933,17 @@ nmf_status nmf_batched_init(int count, const nmf_config* cfgs, const float* cons
                   cudaMemcpyHostToDevice, b->st);
   cudaMemcpyAsync(b->d_gitems[1], gitems[1].data(), sizeof(int2) * gitems[1].size(),
                   cudaMemcpyHostToDevice, b->st);
+  // item-Gram slots: half 0's items (M = n) of every instance, then half 1's
+  {
+    int slot = 0;
+    for (int h = 0; h < 2; ++h)
+      for (int i = 0; i < count; ++i) {
+        inst[i].slot0[h] = slot;
+        slot += (int)ceil_div(inst[i].M[h], (int64_t)kBM);
+      }
+    if ((e = balloc(b, (void**)&b->d_gitem, sizeof(double) * kBR * kBR * (size_t)slot)) != cudaSuccess)
+      return fail_cuda(e, "cudaMalloc");
+  }
   // device tables
   if ((e = balloc(b, (void**)&b->d_inst, sizeof(BatchInst) * count)) != cudaSuccess ||
       (e = balloc(b, (void**)&b->d_maps, sizeof(CUtensorMap) * maps.size())) != cudaSuccess ||
@@ -912,6 +1040,7 @@ nmf_status nmf_batched_init(int count, const nmf_config* cfgs, const float* cons
     b->schedule = cands[c].first + "/" + std::to_string(cands[c].second);
     return cudaSuccess;
   };
+  if ((e = start_gram(b)) != cudaSuccess) return fail_cuda(e, "gram");
   if (chosen < 0) {
     // Tune on copies of the factors so that the caller's starting point is kept.
     std::vector<float*> wsave(count), hsave(count);
@@ -953,6 +1082,7 @@ nmf_status nmf_batched_init(int count, const nmf_config* cfgs, const float* cons
                            B.op_lo[0], B.ldop[0], plane, b->st);
       count_launches(2);
     }
+    if ((e = start_gram(b)) != cudaSuccess) return fail_cuda(e, "gram");
     if (cache) {
       std::ofstream o(cache, std::ios::app);
       o << sig << " " << cands[chosen].first << " " << cands[chosen].second << "\n";
