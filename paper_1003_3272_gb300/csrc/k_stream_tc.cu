@@ -109,7 +109,9 @@ struct TcShape {
   static constexpr int STAGES_RAW = (kSmemMax - DED - 2048) / STAGE;
   static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
   static constexpr int RING = STAGES * STAGE;
-  static constexpr int MAIN = RING > ACC + NSB ? RING : ACC + NSB;  // Acc/Ns reuse the ring
+  static constexpr int DSB = tcepi::kRmax * tcepi::ldd<RPAD>() * 4;  // denominators
+  // Acc, Ns and Ds reuse the ring after the stream
+  static constexpr int MAIN = RING > ACC + NSB + DSB ? RING : ACC + NSB + DSB;
   static constexpr int SMEM = MAIN + DED + 1024;   // + alignment slack
   // Tensor-memory column stride of one accumulator; the block allocates up
   // to 512 columns (it is alone on its SM: its shared memory exceeds half
@@ -404,16 +406,19 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
               make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
       }
     }
+    float* Ds = reinterpret_cast<float*>(smem + Sh::ACC + Sh::NSB);   // [R][RPAD + 4]
+    if (!abort && helper) tcepi::den_to_smem<RPAD>(den, Ds, R, h);
     ptx::tc_fence_before();
     // Cluster barriers are executed the same number of times by every block
     // of a cluster, aborted or not, so no block can wait on a peer forever.
-    cluster.sync();   // every block's partial tile is in its shared memory
+    cluster.sync();   // every block's partial tile (and its Ds) is in shared memory
     if (!abort) {
-      // rows [q R, (q+1) R) of the tile: the S partial tiles summed in rank order
-      tcepi::cluster_sum<RPAD, kThreads>(S, Acc, Ns, q);
+      // rows [q R, (q+1) R) of the tile: the S partial tiles summed in rank
+      // order, and the update of each entry from old, num and den
+      tcepi::cluster_update<RPAD, kThreads>(S, Acc, Ns, Os, Ds, a.ep, q, row0, rows);
     }
-    cluster.sync();   // peers are done reading this block's tile
-    if (!*(volatile int*)&s_abort) tcepi::finish<RPAD, kThreads>(Ns, Os, den, a.ep, R, row0, rows);
+    cluster.sync();   // peers are done reading this block's tile; Ns is complete
+    if (!*(volatile int*)&s_abort) tcepi::store_cols<RPAD, kThreads>(Ns, a.ep, row0, rows);
     // The next tile's copies overwrite this shared memory through the async proxy.
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();

@@ -12,9 +12,10 @@
 //   * for each output tile, the old rows of the factor being updated and the
 //     denominators  den[m,k] = sum_l old[m,l] G[l,k]  (the paper's V_n W_n
 //     W_n^t, resp. V^t V W_n, grouped through G; Section 3.1).
-// After the product lands, the whole block only forms
-//     new[m,k] = old[m,k] * num[m,k] / (den[m,k] + eps)
-// and writes the factor and its operand plane(s).
+// After the product lands, the helpers put the denominators into shared
+// memory and the whole block, while it sums the cluster's partial tiles,
+// forms  new[m,k] = old[m,k] * num[m,k] / (den[m,k] + eps),  then writes the
+// factor and its operand plane(s).
 #pragma once
 
 #include <cooperative_groups.h>
@@ -35,7 +36,7 @@ template <int RPAD> __host__ __device__ constexpr int ldq() { return RPAD + 4; }
 template <int RPAD> __host__ __device__ constexpr int ldo() { return RPAD + 1; }
 
 // Floats of the helpers' dedicated shared memory: staging Qs and old rows Os.
-// (The denominators stay in the helpers' registers.)
+// (The denominators stay in the helpers' registers until the stream ends.)
 template <int RPAD>
 __host__ __device__ constexpr int dedicated_floats() {
   return kQsRows * ldq<RPAD>() + kRmax * ldo<RPAD>();
@@ -108,12 +109,56 @@ __device__ __forceinline__ void helper_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(NH) : "memory");
 }
 
-// Sum, in rank order, of the S partial tiles of a cluster (each block's
-// Acc[128][LDA] in its shared memory) over this block's rows [q R, (q+1) R),
-// R = 128 / S, into Ns[R][LN]: every thread issues all of its distributed
-// shared-memory loads before it adds, so the cluster's round trips overlap.
+// The helpers' denominators into Ds[m][k] (stride ldd = RPAD + 4), once
+// the stream is over (the ring's shared memory is free then).
+template <int RPAD> __host__ __device__ constexpr int ldd();
+template <int RPAD, int NH = kHelpers>
+__device__ void den_to_smem(const DenTile<RPAD, NH>& den, float* Ds, int R, int h) {
+  constexpr int KG = DenTile<RPAD, NH>::KG;
+  constexpr int MG = DenTile<RPAD, NH>::MG;
+  constexpr int NA = DenTile<RPAD, NH>::NA;
+  constexpr int LD = ldd<RPAD>();
+  if (h < 0 || h >= KG * MG) return;
+  const int kg = h % KG, mg = h / KG;
+#pragma unroll
+  for (int a = 0; a < NA; ++a)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int m = mg + (4 * a + i) * MG;
+      if (m < R) {
+        *reinterpret_cast<float4*>(&Ds[m * LD + kg * 8]) =
+            make_float4(den.d[a][i][0], den.d[a][i][1], den.d[a][i][2], den.d[a][i][3]);
+        *reinterpret_cast<float4*>(&Ds[m * LD + kg * 8 + 4]) =
+            make_float4(den.d[a][i][4], den.d[a][i][5], den.d[a][i][6], den.d[a][i][7]);
+      }
+    }
+}
+template <int RPAD, int NH = kHelpers>
+__device__ void den_to_smem(const DenTile8<RPAD, NH>& den, float* Ds, int R, int h) {
+  constexpr int KG = DenTile8<RPAD, NH>::KG;
+  constexpr int MG = DenTile8<RPAD, NH>::MG;
+  constexpr int LD = ldd<RPAD>();
+  if (h < 0 || h >= KG * MG) return;
+  const int kg = h % KG, mg = h / KG;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int m = mg * 8 + i;
+    if (m < R) {
+      *reinterpret_cast<float4*>(&Ds[m * LD + kg * 8]) =
+          make_float4(den.d[i][0], den.d[i][1], den.d[i][2], den.d[i][3]);
+      *reinterpret_cast<float4*>(&Ds[m * LD + kg * 8 + 4]) =
+          make_float4(den.d[i][4], den.d[i][5], den.d[i][6], den.d[i][7]);
+    }
+  }
+}
+
+// The cluster reduction fused with pass 1 of the update: each thread sums
+// four ranks of one row over the S partial tiles (rank order), and at once
+// forms new = (old * num) / (den + eps) from Os and Ds, writing the new
+// values to Ns (for pass 2) and, for a row-major factor (W), to the factor.
 template <int S, int RPAD, int NT>
-__device__ void cluster_sum_s(const float* Acc, float* Ns, int q) {
+__device__ void cluster_update_s(const float* Acc, float* Ns, const float* Os, const float* Ds,
+                                 const EpiArgs& e, int q, int64_t row0, int rows) {
   constexpr int R = 128 / S;
   constexpr int NQ = RPAD / 4;
   constexpr int TOT = R * NQ;
@@ -121,6 +166,9 @@ __device__ void cluster_sum_s(const float* Acc, float* Ns, int q) {
   constexpr int JC = (8 / S) < 1 ? 1 : (8 / S);   // at most 8 loads in flight
   constexpr int LDA = RPAD + 4;
   constexpr int LN = epi_ldn<RPAD>();
+  constexpr int LO = ldo<RPAD>();
+  constexpr int LD = ldd<RPAD>();
+  const int r = e.r;
   cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
 #pragma unroll 1
   for (int j0 = 0; j0 < J; j0 += JC) {
@@ -145,17 +193,34 @@ __device__ void cluster_sum_s(const float* Acc, float* Ns, int q) {
         for (int s = 1; s < S; ++s) {
           sum.x += v[j][s].x; sum.y += v[j][s].y; sum.z += v[j][s].z; sum.w += v[j][s].w;
         }
-        *reinterpret_cast<float4*>(&Ns[m * LN + k4]) = sum;
+        const float nu[4] = {sum.x, sum.y, sum.z, sum.w};
+        float o[4], nv[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) o[t] = Os[m * LO + k4 + t];
+        const float4 dn = *reinterpret_cast<const float4*>(&Ds[m * LD + k4]);
+        const float dv[4] = {dn.x, dn.y, dn.z, dn.w};
+        update8<4>(o, nu, dv, e.eps, nv);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (k4 + t >= r) nv[t] = 0.f;
+        *reinterpret_cast<float4*>(&Ns[m * LN + k4]) = make_float4(nv[0], nv[1], nv[2], nv[3]);
+        if (e.layout == kFactorRowMajor && m < rows) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (k4 + t < r) e.F[(row0 + m) * r + k4 + t] = nv[t];
+        }
       }
     }
   }
 }
 
 template <int RPAD, int NT>
-__device__ void cluster_sum(int S, const float* Acc, float* Ns, int q) {
-  if (S == 2) cluster_sum_s<2, RPAD, NT>(Acc, Ns, q);
-  else if (S == 4) cluster_sum_s<4, RPAD, NT>(Acc, Ns, q);
-  else cluster_sum_s<8, RPAD, NT>(Acc, Ns, q);
+__device__ void cluster_update(int S, const float* Acc, float* Ns, const float* Os,
+                               const float* Ds, const EpiArgs& e, int q, int64_t row0,
+                               int rows) {
+  if (S == 2) cluster_update_s<2, RPAD, NT>(Acc, Ns, Os, Ds, e, q, row0, rows);
+  else if (S == 4) cluster_update_s<4, RPAD, NT>(Acc, Ns, Os, Ds, e, q, row0, rows);
+  else cluster_update_s<8, RPAD, NT>(Acc, Ns, Os, Ds, e, q, row0, rows);
 }
 
 // Pass 2 of an update: the [k][m]-ordered outputs (planes, and H itself) of
@@ -510,56 +575,6 @@ __device__ void compute_den(float* Qs, const float* Os, DenTile<RPAD, NH>& den, 
   }
 }
 
-// new = old * num / (den + eps) for the slice (num in Ns[m][k], stride LN),
-// then the factor and its operand plane(s).  Pass 1 (helpers, their own
-// denominators): new values into Ns, and the row-major factor (W) directly.
-// Pass 2 (every thread of the block, rows fastest): the [k][m]-ordered
-// arrays -- the plane(s) and, for H, the factor.
-template <int RPAD, int NT, int HBASE = kHelperBase, int NH = kHelpers>
-__device__ void finish(float* Ns, const float* Os, const DenTile<RPAD, NH>& den,
-                       const EpiArgs& e, int R, int64_t row0, int rows) {
-  constexpr int LN = epi_ldn<RPAD>();
-  constexpr int LO = ldo<RPAD>();
-  constexpr int KG = DenTile<RPAD, NH>::KG;
-  constexpr int MG = DenTile<RPAD, NH>::MG;
-  constexpr int NA = DenTile<RPAD, NH>::NA;
-  const int r = e.r;
-  const int tid = threadIdx.x;
-  const int h = tid - HBASE;
-  if (h >= 0 && h < KG * MG) {
-    const int kg = h % KG, mg = h / KG;
-#pragma unroll
-    for (int a = 0; a < NA; ++a)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int m = mg + (4 * a + i) * MG;
-        if (m >= rows) continue;
-        float v[8], o[8], nu[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          o[j] = Os[m * LO + kg * 8 + j];
-          nu[j] = Ns[m * LN + kg * 8 + j];
-        }
-        update8(o, nu, den.d[a][i], e.eps, v);
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (kg * 8 + j >= r) v[j] = 0.f;
-#pragma unroll
-        for (int j = 0; j < 8; j += 4)
-          *reinterpret_cast<float4*>(&Ns[m * LN + kg * 8 + j]) =
-              make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-        if (e.layout == kFactorRowMajor) {
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (kg * 8 + j < r) e.F[(row0 + m) * r + kg * 8 + j] = v[j];
-        }
-      }
-  }
-  __syncthreads();
-  store_cols<RPAD, NT>(Ns, e, row0, rows);
-  (void)R;
-}
-
 // compute_den for DenTile8 (ranks above 64).
 template <int RPAD, int NH = kHelpers>
 __device__ void compute_den(float* Qs, const float* Os, DenTile8<RPAD, NH>& den,
@@ -611,49 +626,6 @@ __device__ void compute_den(float* Qs, const float* Os, DenTile8<RPAD, NH>& den,
       }
     }
   }
-}
-
-// finish for DenTile8: as finish(), pass 1 over the helper's 8 x 8 block.
-template <int RPAD, int NT, int HBASE = kHelperBase, int NH = kHelpers>
-__device__ void finish(float* Ns, const float* Os, const DenTile8<RPAD, NH>& den,
-                       const EpiArgs& e, int R, int64_t row0, int rows) {
-  constexpr int LN = epi_ldn<RPAD>();
-  constexpr int LO = ldo<RPAD>();
-  constexpr int KG = DenTile8<RPAD, NH>::KG;
-  constexpr int MG = DenTile8<RPAD, NH>::MG;
-  const int r = e.r;
-  const int tid = threadIdx.x;
-  const int h = tid - HBASE;
-  if (h >= 0 && h < KG * MG) {
-    const int kg = h % KG, mg = h / KG;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int m = mg * 8 + i;
-      if (m >= rows) continue;
-      float v[8], o[8], nu[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        o[j] = Os[m * LO + kg * 8 + j];
-        nu[j] = Ns[m * LN + kg * 8 + j];
-      }
-      update8(o, nu, den.d[i], e.eps, v);
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        if (kg * 8 + j >= r) v[j] = 0.f;
-#pragma unroll
-      for (int j = 0; j < 8; j += 4)
-        *reinterpret_cast<float4*>(&Ns[m * LN + kg * 8 + j]) =
-            make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-      if (e.layout == kFactorRowMajor) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (kg * 8 + j < r) e.F[(row0 + m) * r + kg * 8 + j] = v[j];
-      }
-    }
-  }
-  __syncthreads();
-  store_cols<RPAD, NT>(Ns, e, row0, rows);
-  (void)R;
 }
 
 // Variant for kernels with shared memory to spare: den into Ds[m][k]
