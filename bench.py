@@ -181,7 +181,8 @@ def algorithmic(prec, p, n, r):
     return bytes_, flops
 
 
-TC_SOURCES = ["k_stream_tc.cu", "tc_epi.cuh", "tc_ptx.cuh", "epilogue.cuh", "tc.cuh"]
+TC_SOURCES = ["k_stream_tc.cu", "tc_epi.cuh", "tc_ptx.cuh", "epilogue.cuh", "tc.cuh",
+              "nmf_internal.cuh"]
 
 
 def kernel_source_digest():
