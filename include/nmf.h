@@ -182,6 +182,18 @@ void nmf_batched_destroy(nmf_batch* b);
 nmf_status nmf_gram_noalloc(const float* F, int32_t layout, int64_t M, int64_t ldf, int32_t r,
                             double* G_out, void* stream);
 
+/* ---- Failure-detection test hook ------------------------------------------
+ * No counterpart in the paper.  Every device-side wait of the library is
+ * bounded (about 1.5 s); when one expires the kernel records NMF_ETIMEOUT in
+ * the context's error word, skips the rest of its work (the factors keep
+ * their previous values) and returns, and the next synchronising call
+ * (nmf_objective, nmf_run, nmf_read_gram, nmf_solve) reports NMF_ETIMEOUT.
+ * This hook makes that happen on purpose for the next half step: it gives
+ * the launch's grid-wide publication waits a target the device counter
+ * never reaches, so that every block's wait runs out (about 3 s in all).
+ * The context stays usable afterwards.  NMF_EINVAL for ctx == NULL.        */
+nmf_status nmf_test_expire_next_wait(nmf_ctx* ctx);
+
 /* ---- Self-check of the update's division ----------------------------------
  * No counterpart in the paper.  The update new = (old * num) / (den + eps)
  * (Eqs. (3.3)-(3.4)) divides with IEEE round-to-nearest; the kernels do so by

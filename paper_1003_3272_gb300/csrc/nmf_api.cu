@@ -91,6 +91,7 @@ struct nmf_ctx {
   int gcount[2] = {0, 0};
   unsigned long long* gctr = nullptr;     // grid-wide counter of the tensor-core kernel
   unsigned long long gctr_host = 0;       // its value after every launch so far
+  unsigned long long gctr_skew = 0;       // test hook: added to the next launch's target
   float* GWpad = nullptr; float* GHpad = nullptr;   // rpad x rpad Grams (tensor-core form)
   double* tc_gpart = nullptr;             // tensor-core prologue partials (one per block)
   // objective
@@ -413,7 +414,8 @@ nmf_status run_half(nmf_ctx* c, int which) {
     g.Gpad = other == 0 ? c->GWpad : c->GHpad;
     g.G64 = other == 0 ? c->GW64 : c->GH64;
     g.ctr = c->gctr;
-    g.base = c->gctr_host;
+    g.base = c->gctr_host + c->gctr_skew;   // skew: only from nmf_test_expire_next_wait
+    c->gctr_skew = 0;
     c->gctr_host += 2ull * (unsigned long long)h.tc.grid;
     // timed per nmf_step (events between launches would break the
     // programmatic dependent launch chain); a lone half step times itself
@@ -597,6 +599,12 @@ nmf_status nmf_solve(const nmf_config* cfg, const float* V, float* W, float* H, 
   cleanup();
   if (s != NMF_OK) g_last_error = why;
   return s;
+}
+
+nmf_status nmf_test_expire_next_wait(nmf_ctx* c) {
+  if (!c) { set_err(nullptr, "ctx is NULL"); return NMF_EINVAL; }
+  c->gctr_skew = 1ull << 40;   // a counter value no launch reaches
+  return NMF_OK;
 }
 
 nmf_status nmf_restart(nmf_ctx* c, uint64_t seed) {

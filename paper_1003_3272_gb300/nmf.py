@@ -45,7 +45,7 @@ EXPORTS = [
     "nmf_batched_step", "nmf_batched_objective", "nmf_batched_destroy",
     "nmf_status_str", "nmf_last_error", "nmf_version", "nmf_restart",
     "nmf_kernel_launches", "nmf_profile_enable", "nmf_profile_read", "nmf_gram_noalloc",
-    "nmf_selfcheck_div",
+    "nmf_selfcheck_div", "nmf_test_expire_next_wait",
 ]
 
 _lib = None
@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "nmf_gram_noalloc": ([c_p, i32, i64, i64, i32, c_p, c_p], ctypes.c_int),
         "nmf_selfcheck_div": ([i64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
                                ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "nmf_test_expire_next_wait": ([c_p], ctypes.c_int),
         "nmf_profile_enable": ([c_p, ctypes.c_int], ctypes.c_int),
         "nmf_profile_read": ([c_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -195,6 +196,11 @@ class NMF:
         _check(self.lib.nmf_run(self.ctx, int(max_iters), float(tol), int(check_every),
                                 ctypes.byref(done), ctypes.byref(f)), self.ctx)
         return done.value, f.value
+
+    def expire_next_wait(self):
+        """Test hook: the next half step's grid-wide waits run out (about
+        3 s); the next synchronising call raises NMFError(ETIMEOUT)."""
+        _check(self.lib.nmf_test_expire_next_wait(self.ctx), self.ctx)
 
     def restart(self, seed: int):
         """Algorithm 1's seeded start on the same V (no allocation)."""

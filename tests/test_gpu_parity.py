@@ -239,3 +239,33 @@ def test_update_division_is_the_ieee_division():
     mism, quick = nmf.selfcheck_div(count, seed=7)
     assert mism == 0
     assert quick > (64 << 23)          # the sweep and most random pairs took the quick form
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_expired_device_wait_is_reported_and_the_context_recovers(prec):
+    """Failure detection without a fault: the next half step's grid-wide
+    waits get a target the device counter never reaches; every block's
+    bounded wait runs out, the launch skips its update and records
+    NMF_ETIMEOUT, the next synchronising call reports it, and the context
+    then works on (the skipped half step left the factors as they were)."""
+    import time
+    from paper_1003_3272_gb300 import nmf
+    pr = synth.faces()
+    V, W, H = to_dev(pr.V), to_dev(pr.W0), to_dev(pr.H0)
+    with nmf.NMF(V, W, H, eps=pr.eps, prec=prec) as m:
+        m.step(2)
+        f2 = m.objective()
+        W2, H2 = to_host(W), to_host(H)
+        m.expire_next_wait()
+        t0 = time.time()
+        m.half_step(0)                     # H update: its waits run out
+        with pytest.raises(nmf.NMFError) as ei:
+            m.objective()
+        assert ei.value.status == nmf.ETIMEOUT
+        assert time.time() - t0 < 60
+        np.testing.assert_array_equal(to_host(H), H2)   # the update was skipped
+        assert m.objective() == f2                      # state as before, no error left
+        m.step(2)
+        f4 = m.objective()
+        assert np.isfinite(f4) and f4 <= f2
+    np.testing.assert_array_equal(to_host(W).shape, W2.shape)
