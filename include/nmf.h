@@ -23,8 +23,9 @@
  *   - The caller owns V, W and H.  V must stay alive and unchanged for the
  *     life of a context; W and H are read and updated in place.
  *   - The library owns its workspaces (operand copies of V in the layout and
- *     precision of the chosen arithmetic, split-K partial sums, Gram
- *     matrices, objective partials) and frees them in nmf_destroy.
+ *     precision of the chosen arithmetic, factor operand planes, Gram
+ *     matrices and their partials, objective partials) and frees them in
+ *     nmf_destroy.
  *   - Errors are reported only through the return code (never by exception,
  *     abort or device trap).  nmf_last_error() gives a one-line reason.
  *   - A context is bound to one CUDA stream and is not thread-safe; use one
