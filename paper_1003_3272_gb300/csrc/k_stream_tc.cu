@@ -94,14 +94,25 @@ __host__ __device__ constexpr int stage_kbytes() {
   return (PREC == NMF_BF16X3 && RPAD >= 80) ? 64 : 128;
 }
 
+// Sub-blocks of K per stage: single-plane forms (TF32, BF16) up to rank 64
+// carry two 128-byte k-blocks per stage, so that a stage moves as many bytes
+// as a split-BF16x3 stage (the per-stage cost of the pipeline is then paid
+// half as often).
+template <int PREC, int RPAD>
+__host__ __device__ constexpr int stage_subs() {
+  return (PREC != NMF_BF16X3 && RPAD <= 64) ? 2 : 1;
+}
+
 template <int PREC, int RPAD>
 struct TcShape {
   static constexpr int XPL = PrecTraits<PREC>::XPL;
   static constexpr int KBY = stage_kbytes<PREC, RPAD>();
-  static constexpr int KB = KBY / (PREC == NMF_TF32 ? 4 : 2);   // K elements per stage
+  static constexpr int NSUB = stage_subs<PREC, RPAD>();
+  static constexpr int KB = KBY / (PREC == NMF_TF32 ? 4 : 2);   // K elements per sub-block
   static constexpr int X_BYTES = kBM * KBY;       // one plane of X: 128 rows x KBY
   static constexpr int Y_BYTES = RPAD * KBY;      // one plane of Y
-  static constexpr int STAGE = XPL * (X_BYTES + Y_BYTES);
+  static constexpr int SUB = XPL * (X_BYTES + Y_BYTES);   // one sub-block: X planes, Y planes
+  static constexpr int STAGE = NSUB * SUB;
   static constexpr int LDA = RPAD + 4;            // accumulator tile row stride (floats)
   static constexpr int ACC = kBM * LDA * 4;       // partial accumulator tile
   static constexpr int NSB = tcepi::kRmax * epi_ldn<RPAD>() * 4;   // reduced slice
@@ -144,7 +155,8 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
   using Sh = TcShape<PREC, RPAD>;
   constexpr int STAGES = Sh::STAGES;
   constexpr int KB = Sh::KB;
-  constexpr int KPB = 128 / Sh::KBY;   // stages per block of the blocked copy
+  constexpr int NSUB = Sh::NSUB;
+  constexpr int KPB = 128 / Sh::KBY;   // sub-blocks per block of the blocked copy
   constexpr bool X3 = PREC == NMF_BF16X3;
   constexpr uint32_t IDESC = ptx::idesc(PrecTraits<PREC>::FMT, kBM, RPAD);
   constexpr int LDA = Sh::LDA;
@@ -173,12 +185,14 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
   float* Os = Qs + tcepi::kQsRows * tcepi::ldq<RPAD>();
   tcepi::DenFor<RPAD> den;
 
-  auto x_addr = [&](int s, int plane) { return sbase + s * Sh::STAGE + plane * Sh::X_BYTES; };
+  auto x_addr = [&](int s, int plane, int sub = 0) {
+    return sbase + s * Sh::STAGE + sub * Sh::SUB + plane * Sh::X_BYTES;
+  };
   auto sdesc = [](uint32_t addr) {
     return Sh::KBY == 128 ? ptx::sdesc_sw128(addr) : ptx::sdesc_sw64(addr);
   };
-  auto y_addr = [&](int s, int plane) {
-    return sbase + s * Sh::STAGE + Sh::XPL * Sh::X_BYTES + plane * Sh::Y_BYTES;
+  auto y_addr = [&](int s, int plane, int sub = 0) {
+    return sbase + s * Sh::STAGE + sub * Sh::SUB + Sh::XPL * Sh::X_BYTES + plane * Sh::Y_BYTES;
   };
 
   if (threadIdx.x == 0) {
@@ -205,7 +219,7 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
   // K range of this block (same for every tile).
   const int64_t kbeg = (int64_t)q * a.kper;
   const int64_t kend = min(a.K, kbeg + a.kper);
-  const int nkb = kbeg < kend ? (int)ceil_div(kend - kbeg, KB) : 0;
+  const int nkb = kbeg < kend ? (int)ceil_div(kend - kbeg, (int64_t)KB * NSUB) : 0;   // stages
   const int R = kBM / S;
 
   // ---- helpers, prologue: old rows of the first tile, then the Gram of the
@@ -262,11 +276,14 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
         for (int kb = 0; kb < pre; ++kb) {
           const uint32_t fb = ptx::smem_u32(&full_bar[kb]);
           ptx::mbar_expect_tx(fb, Sh::STAGE);
-          const int64_t hk = kbeg / KB + kb;
-          const int32_t xb = (int32_t)((int64_t)tile * a.nkbt + hk / KPB);
-          const int32_t xk = (int32_t)(hk % KPB) * KB;
-          ptx::tma_load_3d(x_addr(kb, 0), &tx_hi, xk, 0, xb, fb);
-          if (X3) ptx::tma_load_3d(x_addr(kb, 1), &tx_lo, xk, 0, xb, fb);
+#pragma unroll
+          for (int sub = 0; sub < NSUB; ++sub) {
+            const int64_t hk = kbeg / KB + (int64_t)kb * NSUB + sub;
+            const int32_t xb = (int32_t)((int64_t)tile * a.nkbt + hk / KPB);
+            const int32_t xk = (int32_t)(hk % KPB) * KB;
+            ptx::tma_load_3d(x_addr(kb, 0, sub), &tx_hi, xk, 0, xb, fb);
+            if (X3) ptx::tma_load_3d(x_addr(kb, 1, sub), &tx_lo, xk, 0, xb, fb);
+          }
         }
         ptx::pdl_wait();
         // Our own predecessor is complete: the next half step may now be
@@ -275,9 +292,12 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
         ptx::pdl_launch_dependents();
         for (int kb = 0; kb < pre; ++kb) {
           const uint32_t fb = ptx::smem_u32(&full_bar[kb]);
-          const int32_t kc = (int32_t)(kbeg + (int64_t)kb * KB);
-          ptx::tma_load_2d(y_addr(kb, 0), &ty_hi, kc, 0, fb);
-          if (X3) ptx::tma_load_2d(y_addr(kb, 1), &ty_lo, kc, 0, fb);
+#pragma unroll
+          for (int sub = 0; sub < NSUB; ++sub) {
+            const int32_t kc = (int32_t)(kbeg + ((int64_t)kb * NSUB + sub) * KB);
+            ptx::tma_load_2d(y_addr(kb, 0, sub), &ty_hi, kc, 0, fb);
+            if (X3) ptx::tma_load_2d(y_addr(kb, 1, sub), &ty_lo, kc, 0, fb);
+          }
         }
         issued = pre;
       }
@@ -292,15 +312,18 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
         if (*(volatile int*)&s_abort) break;
         const uint32_t fb = ptx::smem_u32(&full_bar[s]);
         ptx::mbar_expect_tx(fb, Sh::STAGE);
-        const int32_t kc = (int32_t)(kbeg + (int64_t)kb * KB);
-        // X block (tile, k-block) of the tile-blocked copy (or its half)
-        const int64_t hk = kbeg / KB + kb;
-        const int32_t xb = (int32_t)((int64_t)tile * a.nkbt + hk / KPB);
-        const int32_t xk = (int32_t)(hk % KPB) * KB;
-        ptx::tma_load_3d(x_addr(s, 0), &tx_hi, xk, 0, xb, fb);
-        if (X3) ptx::tma_load_3d(x_addr(s, 1), &tx_lo, xk, 0, xb, fb);
-        ptx::tma_load_2d(y_addr(s, 0), &ty_hi, kc, 0, fb);
-        if (X3) ptx::tma_load_2d(y_addr(s, 1), &ty_lo, kc, 0, fb);
+#pragma unroll
+        for (int sub = 0; sub < NSUB; ++sub) {
+          // X block (tile, k-block) of the tile-blocked copy (or its half)
+          const int64_t hk = kbeg / KB + (int64_t)kb * NSUB + sub;
+          const int32_t kc = (int32_t)(hk * KB);
+          const int32_t xb = (int32_t)((int64_t)tile * a.nkbt + hk / KPB);
+          const int32_t xk = (int32_t)(hk % KPB) * KB;
+          ptx::tma_load_3d(x_addr(s, 0, sub), &tx_hi, xk, 0, xb, fb);
+          if (X3) ptx::tma_load_3d(x_addr(s, 1, sub), &tx_lo, xk, 0, xb, fb);
+          ptx::tma_load_2d(y_addr(s, 0, sub), &ty_hi, kc, 0, fb);
+          if (X3) ptx::tma_load_2d(y_addr(s, 1, sub), &ty_lo, kc, 0, fb);
+        }
         issued = kb + 1;
       }
       // Drain: the last load issued into each stage must have landed.
@@ -331,19 +354,21 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
         if (*(volatile int*)&s_abort) break;
         ptx::tc_fence_after();
 #pragma unroll
+        for (int sub = 0; sub < NSUB; ++sub)
+#pragma unroll
         for (int kk = 0; kk < Sh::KBY / 32; ++kk) {
-          const uint64_t ah = sdesc(x_addr(s, 0) + kk * 32);
-          const uint64_t bh = sdesc(y_addr(s, 0) + kk * 32);
+          const uint64_t ah = sdesc(x_addr(s, 0, sub) + kk * 32);
+          const uint64_t bh = sdesc(y_addr(s, 0, sub) + kk * 32);
           const uint32_t tacc = tmem + (uint32_t)(ai * Sh::CS);
-          const uint32_t acc = (kb >= a.nacc || kk != 0) ? 1u : 0u;
+          const uint32_t acc = (kb >= a.nacc || sub != 0 || kk != 0) ? 1u : 0u;
           if (PREC == NMF_TF32) {
             ptx::mma_tf32(tacc, ah, bh, IDESC, acc);
           } else {
             ptx::mma_bf16(tacc, ah, bh, IDESC, acc);
             if (X3) {
-              const uint64_t al = sdesc(x_addr(s, 1) + kk * 32);
-              const uint64_t bl = sdesc(y_addr(s, 1) + kk * 32);
-              ptx::mma_bf16(tcross, ah, bl, IDESC, (kb | kk) != 0);
+              const uint64_t al = sdesc(x_addr(s, 1, sub) + kk * 32);
+              const uint64_t bl = sdesc(y_addr(s, 1, sub) + kk * 32);
+              ptx::mma_bf16(tcross, ah, bl, IDESC, (kb | sub | kk) != 0);
               ptx::mma_bf16(tcross, al, bh, IDESC, 1);
             }
           }
@@ -571,7 +596,9 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
   // ranks above 64 (see stage_kbytes)
   const int kbytes = (prec == NMF_BF16X3 && pl.rpad >= 80) ? 64 : 128;
   const int esz = (prec == NMF_TF32 || prec == NMF_FP32) ? 4 : 2;
-  pl.kblock = kbytes / esz;
+  // sub-blocks per stage (see stage_subs)
+  const int nsub = (prec == NMF_TF32 || prec == NMF_BF16) && pl.rpad <= 64 ? 2 : 1;
+  pl.kblock = nsub * kbytes / esz;   // K elements per pipeline stage
   pl.M = M; pl.K = K; pl.r = r;
   pl.tiles = (int)ceil_div(M, kBM);
   if (M > INT32_MAX || K > INT32_MAX) { if (err) *err = "size exceeds TMA coordinates"; return NMF_EINVAL; }
@@ -594,7 +621,7 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
   // reduction and update, a few microseconds growing with the rank), times
   // the rounds of tiles; ties go to the most blocks at work.
   const int xpl = prec == NMF_BF16X3 ? 2 : 1;
-  double stage_us = 128.0 * kbytes * xpl / 44000.0;   // ~6.7 TB/s over 152 SMs
+  double stage_us = 128.0 * kbytes * xpl * nsub / 44000.0;   // ~6.7 TB/s over 152 SMs
   if (prec == NMF_FP32)
     stage_us = std::max(stage_us, 128.0 * pl.kblock * pl.rpad / (128.0 * 1900.0 * 0.5));
   const double epi_us = 3.0 + pl.rpad / 16.0;
@@ -641,7 +668,7 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
     const int cs = pl.rpad <= 32 ? 32 : (pl.rpad <= 64 ? 64 : 128);
     const int cross = prec == NMF_BF16X3 ? 1 : 0;
     const int amax = (512 / cs - cross) < 8 ? 512 / cs - cross : 8;
-    const int64_t adds = (pl.kchunk / pl.kblock) * (kbytes / 32);   // MMAs per stage
+    const int64_t adds = (pl.kchunk / pl.kblock) * nsub * (kbytes / 32);   // MMAs per stage
     int na = (int)ceil_div(adds, 256);
     pl.nacc = na < 1 ? 1 : (na > amax ? amax : na);
     int cols = 32;
