@@ -130,6 +130,18 @@ nmf_status nmf_objective(nmf_ctx* ctx, double* f_out);
 nmf_status nmf_run(nmf_ctx* ctx, int max_iters, double tol, int check_every,
                    int* iters_done, double* f_out);
 
+/* nmf_run with the loop on the device: one CUDA graph whose while-node runs
+ * `check_every` iterations, the objective and the stopping test per round;
+ * the test kernel decides whether another round runs, so the host waits
+ * once for the whole run instead of once per test.  Same arguments, same
+ * iterates, *iters_done and *f_out as nmf_run (the tests take the same
+ * float64 operations).  The graph is built on the first call for a given
+ * check_every and kept with the context (captured on a private stream of
+ * the context; the launch and the final copies use the context's stream).
+ * Synchronises.  NMF_ECUDA if the driver cannot build the graph.           */
+nmf_status nmf_converge(nmf_ctx* ctx, int max_iters, double tol, int check_every,
+                        int* iters_done, double* f_out);
+
 /* Restart from Algorithm 1's seeded start on the same V (multiple random
  * starts): rebuild V's operand copies (one pass over V), draw W and H iid
  * uniform(0,1) from `seed` exactly as init_from_seed does, and re-form the

@@ -356,6 +356,34 @@ __global__ void k_sum_partials(const double* __restrict__ partials, int nparts,
   if (threadIdx.x == 0) *out = red[0];
 }
 
+// Section 3's stopping rule, |f_k - f_{k-1}| / (|f_{k-1}| + 1) < tol, taken
+// in float64 with the same operations as the host-side loop (nmf_run), so
+// both stop after the same iteration.
+__global__ void k_run_init(RunState* s, const double* __restrict__ f_dev, int max_iters,
+                           double tol) {
+  const double f = *f_dev;
+  s->f_prev = f;
+  s->f = f;
+  s->tol = tol;
+  s->done = 0;
+  s->checks = 0;
+  s->stop = 0;
+  s->max_iters = max_iters;
+}
+
+__global__ void k_run_test(RunState* s, const double* __restrict__ f_dev, int iters,
+                           cudaGraphConditionalHandle loop) {
+  const double f = *f_dev, fp = s->f_prev;
+  s->done += iters;
+  s->checks += 1;
+  s->f = f;
+  const bool conv = s->tol > 0.0 && fabs(f - fp) / (fabs(fp) + 1.0) < s->tol;
+  if (conv) s->stop = 1;
+  else s->f_prev = f;
+  const bool more = !conv && s->max_iters - s->done >= iters;
+  cudaGraphSetConditional(loop, more ? 1u : 0u);
+}
+
 inline unsigned grid_for(int64_t total, int threads, unsigned cap = 152u * 16u) {
   const int64_t g = ceil_div(total, threads);
   return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
@@ -415,6 +443,18 @@ cudaError_t launch_gram_reduce(const float* gram_part, int tiles, int r, float* 
                                double* G64, cudaStream_t st) {
   const int rr = r * r;
   k_gram_reduce<<<(unsigned)ceil_div(rr, 8), 256, 0, st>>>(gram_part, tiles, r, G32, G64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_run_init(RunState* s, const double* f_dev, int max_iters, double tol,
+                            cudaStream_t st) {
+  k_run_init<<<1, 1, 0, st>>>(s, f_dev, max_iters, tol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_run_test(RunState* s, const double* f_dev, int iters,
+                            cudaGraphConditionalHandle loop, cudaStream_t st) {
+  k_run_test<<<1, 1, 0, st>>>(s, f_dev, iters, loop);
   return cudaGetLastError();
 }
 

@@ -52,7 +52,8 @@ struct F32Params {
   float* Gpad;
   double* G64;
   unsigned long long* ctr;
-  unsigned long long base;
+  unsigned long long unit;   // every launch adds 2 * unit (see k_stream_tc.cu)
+  unsigned long long skew;
   int* err;
 };
 
@@ -90,6 +91,18 @@ __device__ __forceinline__ bool wait_counter(const unsigned long long* ctr,
     if (ptx::globaltimer() - t0 > kWaitLimitNs) return false;
   }
   return true;
+}
+
+// Counter protocol of the tensor-core kernel: each launch adds 2 * unit, so
+// the launch's base is the multiple of 2 * unit below the value a block reads
+// after griddepcontrol.wait and before its own first add.
+__device__ __forceinline__ unsigned long long launch_base(const unsigned long long* ctr,
+                                                          unsigned long long unit) {
+  const unsigned long long v = ld_acquire(ctr);
+  return v - v % (2ull * unit);
+}
+__device__ __forceinline__ unsigned long long phase_add(int grid, unsigned long long unit) {
+  return blockIdx.x == 0 ? 1ull + unit - (unsigned long long)grid : 1ull;
 }
 
 template <int RPAD>
@@ -144,6 +157,7 @@ k_stream_f32(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUt
   if (helper) {
     const int G = gridDim.x;
     ptx::pdl_wait();
+    const unsigned long long base = h == 0 ? launch_base(a.ctr, a.unit) + a.skew : 0ull;
     if (cid < a.tiles) {
       const int64_t row0 = (int64_t)cid * kBM + (int64_t)q * R;
       const int rows = (int)max((int64_t)0, min((int64_t)R, a.M - row0));
@@ -155,8 +169,8 @@ k_stream_f32(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUt
                            a.gpart + (int64_t)blockIdx.x * a.r * a.r, h);
     __threadfence();
     tcepi::helper_sync<kNH>();
-    if (h == 0) atomicAdd(a.ctr, 1ull);
-    if (h == 0 && !wait_counter(a.ctr, a.base + (unsigned long long)G)) atomicExch(&s_abort, 1);
+    if (h == 0) atomicAdd(a.ctr, phase_add(G, a.unit));
+    if (h == 0 && !wait_counter(a.ctr, base + a.unit)) atomicExch(&s_abort, 1);
     tcepi::helper_sync<kNH>();
     if (!*(volatile int*)&s_abort) {
       const int rr = a.r * a.r;
@@ -167,9 +181,8 @@ k_stream_f32(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUt
     }
     __threadfence();
     tcepi::helper_sync<kNH>();
-    if (h == 0) atomicAdd(a.ctr, 1ull);
-    if (h == 0 && !wait_counter(a.ctr, a.base + 2ull * (unsigned long long)G))
-      atomicExch(&s_abort, 1);
+    if (h == 0) atomicAdd(a.ctr, phase_add(G, a.unit));
+    if (h == 0 && !wait_counter(a.ctr, base + 2ull * a.unit)) atomicExch(&s_abort, 1);
     tcepi::helper_sync<kNH>();
   }
 
@@ -368,7 +381,7 @@ cudaError_t f32_launch(const TcPlan& pl, const EpiArgs& ep, const TcGram& gr, in
   prm.ep = ep;
   prm.Q = gr.Q; prm.q_layout = gr.q_layout; prm.ldq = gr.ldq; prm.QM = gr.QM;
   prm.gpart = gr.gpart; prm.Gpad = gr.Gpad; prm.G64 = gr.G64;
-  prm.ctr = gr.ctr; prm.base = gr.base;
+  prm.ctr = gr.ctr; prm.unit = gr.unit; prm.skew = gr.skew;
   prm.err = err;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)pl.grid, 1, 1);

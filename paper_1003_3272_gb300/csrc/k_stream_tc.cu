@@ -75,7 +75,8 @@ struct TcParams {
   float* Gpad;           // [RPAD][RPAD] float32 Gram, zero padded
   double* G64;           // [r][r] float64 Gram
   unsigned long long* ctr;     // grid-wide publication counter (monotone)
-  unsigned long long base;     // its value before this launch
+  unsigned long long unit;     // every launch adds 2 * unit to it (unit >= grid)
+  unsigned long long skew;     // added to the wait targets (0; test hook)
   int* err;              // device error word
 };
 
@@ -145,6 +146,21 @@ __device__ __forceinline__ bool wait_counter(const unsigned long long* ctr,
     if (ptx::globaltimer() - t0 > kWaitLimitNs) return false;
   }
   return true;
+}
+
+// The grid-wide counter carries no host-tracked state, so that a CUDA graph
+// can replay the launch: every launch adds exactly 2 * unit (block 0 adds
+// 1 + unit - grid in each of the two phases, every other block 1), launch
+// bases are therefore multiples of 2 * unit, and a block reads its launch's
+// base after the previous launch has completed (griddepcontrol.wait) and
+// before its own first add, when the counter lies in [base, base + unit).
+__device__ __forceinline__ unsigned long long launch_base(const unsigned long long* ctr,
+                                                          unsigned long long unit) {
+  const unsigned long long v = ld_acquire(ctr);
+  return v - v % (2ull * unit);
+}
+__device__ __forceinline__ unsigned long long phase_add(int grid, unsigned long long unit) {
+  return blockIdx.x == 0 ? 1ull + unit - (unsigned long long)grid : 1ull;
 }
 
 template <int PREC, int RPAD>
@@ -228,6 +244,7 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
   if (helper) {
     const int G = gridDim.x;
     ptx::pdl_wait();   // the factors of the previous half step are final
+    const unsigned long long base = h == 0 ? launch_base(a.ctr, a.unit) + a.skew : 0ull;
     if (cid < a.tiles) {
       const int64_t row0 = (int64_t)cid * kBM + (int64_t)q * R;
       const int rows = (int)max((int64_t)0, min((int64_t)R, a.M - row0));
@@ -239,8 +256,8 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
                            a.gpart + (int64_t)blockIdx.x * a.r * a.r, h);
     __threadfence();
     tcepi::helper_sync();
-    if (h == 0) atomicAdd(a.ctr, 1ull);
-    if (h == 0 && !wait_counter(a.ctr, a.base + (unsigned long long)G)) atomicExch(&s_abort, 1);
+    if (h == 0) atomicAdd(a.ctr, phase_add(G, a.unit));
+    if (h == 0 && !wait_counter(a.ctr, base + a.unit)) atomicExch(&s_abort, 1);
     tcepi::helper_sync();
     if (!*(volatile int*)&s_abort) {
       const int rr = a.r * a.r;
@@ -251,9 +268,8 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
     }
     __threadfence();
     tcepi::helper_sync();
-    if (h == 0) atomicAdd(a.ctr, 1ull);
-    if (h == 0 && !wait_counter(a.ctr, a.base + 2ull * (unsigned long long)G))
-      atomicExch(&s_abort, 1);
+    if (h == 0) atomicAdd(a.ctr, phase_add(G, a.unit));
+    if (h == 0 && !wait_counter(a.ctr, base + 2ull * a.unit)) atomicExch(&s_abort, 1);
     tcepi::helper_sync();
   }
 
@@ -705,7 +721,7 @@ cudaError_t tc_launch(const TcPlan& pl, const EpiArgs& ep, const TcGram& gr, int
   prm.Q = gr.Q; prm.q_layout = gr.q_layout; prm.ldq = gr.ldq; prm.QM = gr.QM;
   prm.gpart = gr.gpart;
   prm.Gpad = gr.Gpad; prm.G64 = gr.G64;
-  prm.ctr = gr.ctr; prm.base = gr.base;
+  prm.ctr = gr.ctr; prm.unit = gr.unit; prm.skew = gr.skew;
   prm.err = err;
 
   cudaLaunchConfig_t cfg = {};

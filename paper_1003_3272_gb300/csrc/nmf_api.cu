@@ -89,8 +89,8 @@ struct nmf_ctx {
   // that factor; the matching Gram is their float64 sum.
   float* gpart[2] = {nullptr, nullptr};   // [0] W, [1] H
   int gcount[2] = {0, 0};
-  unsigned long long* gctr = nullptr;     // grid-wide counter of the tensor-core kernel
-  unsigned long long gctr_host = 0;       // its value after every launch so far
+  unsigned long long* gctr = nullptr;     // grid-wide counter of the streaming launches
+  unsigned long long gunit = 0;           // each launch adds 2 x gunit (>= every grid)
   unsigned long long gctr_skew = 0;       // test hook: added to the next launch's target
   float* GWpad = nullptr; float* GHpad = nullptr;   // rpad x rpad Grams (tensor-core form)
   double* tc_gpart = nullptr;             // tensor-core prologue partials (one per block)
@@ -105,6 +105,14 @@ struct nmf_ctx {
   // CUDA-event timing by kind (nmf_profile_*)
   bool prof = false;
   bool in_step = false;       // inside nmf_step (tensor-core launches timed as a group)
+  bool capturing = false;     // recording the convergence graph: no events, no test skew
+  // nmf_converge: the run's device state and the graph of its loop, built
+  // for one check interval and kept until another is asked for
+  RunState* run_dev = nullptr;
+  RunState* run_host = nullptr;   // pinned
+  cudaStream_t cap_st = nullptr;  // private stream the loop body is captured on
+  cudaGraphExec_t conv_exec = nullptr;
+  int conv_k = 0;
   std::vector<cudaEvent_t> ev_pool;
   struct Open { int kind; int launches; cudaEvent_t a, b; };
   std::vector<Open> ev_open;
@@ -161,7 +169,7 @@ struct ProfScope {
   int launches;
   cudaEvent_t a = nullptr, b = nullptr;
   ProfScope(nmf_ctx* c_, int k, int n = 1) : c(c_), kind(k), launches(n) {
-    if (!c->prof || n <= 0) return;
+    if (!c->prof || c->capturing || n <= 0) return;
     a = take_event(c);
     b = take_event(c);
     if (a && b) cudaEventRecord(a, c->st);
@@ -354,7 +362,7 @@ nmf_status build_ctx(nmf_ctx* c) {
   for (int f = 0; f < 2; ++f)
     if ((s = dalloc(c, (void**)&c->gpart[f], gtiles[f] * rr * 4)) != NMF_OK) return s;
   if ((s = dalloc(c, (void**)&c->gctr, sizeof(unsigned long long))) != NMF_OK) return s;
-  c->gctr_host = 0;
+  c->gunit = (unsigned long long)(hh.tc.grid > hw.tc.grid ? hh.tc.grid : hw.tc.grid);
   {
     const size_t rp2 = (size_t)c->rpad * c->rpad;
     if ((s = dalloc(c, (void**)&c->GWpad, rp2 * 4)) != NMF_OK) return s;
@@ -367,6 +375,8 @@ nmf_status build_ctx(nmf_ctx* c) {
   if ((s = dalloc(c, (void**)&c->err_dev, sizeof(int))) != NMF_OK) return s;
   CK(cudaMallocHost((void**)&c->f_host, 8), "cudaMallocHost");
   CK(cudaMallocHost((void**)&c->err_host, sizeof(int)), "cudaMallocHost");
+  if ((s = dalloc(c, (void**)&c->run_dev, sizeof(RunState))) != NMF_OK) return s;
+  CK(cudaMallocHost((void**)&c->run_host, sizeof(RunState)), "cudaMallocHost");
 
   return prepare(c, c->cfg.init_from_seed != 0, c->cfg.seed);
 }
@@ -377,6 +387,9 @@ void free_ctx(nmf_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
   if (c->f_host) cudaFreeHost(c->f_host);
   if (c->err_host) cudaFreeHost(c->err_host);
+  if (c->run_host) cudaFreeHost(c->run_host);
+  if (c->conv_exec) cudaGraphExecDestroy(c->conv_exec);
+  if (c->cap_st) cudaStreamDestroy(c->cap_st);
   for (auto& it : c->ev_open) { cudaEventDestroy(it.a); cudaEventDestroy(it.b); }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   (void)cudaGetLastError();
@@ -414,14 +427,17 @@ nmf_status run_half(nmf_ctx* c, int which) {
     g.Gpad = other == 0 ? c->GWpad : c->GHpad;
     g.G64 = other == 0 ? c->GW64 : c->GH64;
     g.ctr = c->gctr;
-    g.base = c->gctr_host + c->gctr_skew;   // skew: only from nmf_test_expire_next_wait
-    c->gctr_skew = 0;
-    c->gctr_host += 2ull * (unsigned long long)h.tc.grid;
+    g.unit = c->gunit;
+    g.skew = 0;
+    if (!c->capturing) {   // skew: only from nmf_test_expire_next_wait
+      g.skew = c->gctr_skew;
+      c->gctr_skew = 0;
+    }
     // timed per nmf_step (events between launches would break the
     // programmatic dependent launch chain); a lone half step times itself
     ProfScope ps(c, 0, c->in_step ? 0 : 1);
     CK(tc_launch(h.tc, h.ep, g, c->err_dev, c->st), "stream (tensor)");
-    launched(1);
+    if (!c->capturing) launched(1);   // graph replays are counted by nmf_converge
   }
   return NMF_OK;
 }
@@ -534,6 +550,106 @@ nmf_status nmf_run(nmf_ctx* c, int max_iters, double tol, int check_every, int* 
     // Section 3's rule: |f_k - f_{k-1}| / (|f_{k-1}| + 1) < tol
     if (tol > 0.0 && std::fabs(f - f_prev) / (std::fabs(f_prev) + 1.0) < tol) break;
     f_prev = f;
+  }
+  if (iters_done) *iters_done = done;
+  if (f_out) *f_out = f;
+  return NMF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The loop of nmf_converge as one CUDA graph: a while-node whose body runs
+// k iterations (2k streaming launches), the objective and the stopping
+// test; the test kernel sets the node's condition, so the whole run to
+// convergence is one graph launch with no host round trip.
+nmf_status build_conv_graph(nmf_ctx* c, int k) {
+  if (c->conv_exec && c->conv_k == k) return NMF_OK;
+  if (c->conv_exec) { cudaGraphExecDestroy(c->conv_exec); c->conv_exec = nullptr; }
+  if (!c->cap_st) CK(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking), "stream");
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0), "graph create");
+  cudaGraphConditionalHandle loop;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};   // the rest zero
+  np.conditional.handle = loop;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  cudaGraph_t body = e == cudaSuccess ? np.conditional.phGraph_out[0] : nullptr;
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(c->cap_st, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed);
+  nmf_status s = NMF_OK;
+  if (e == cudaSuccess) {
+    cudaStream_t user = c->st;
+    c->st = c->cap_st;
+    c->capturing = true;
+    const int first = c->cfg.order == NMF_ORDER_H_FIRST ? 0 : 1;
+    for (int it = 0; it < k && s == NMF_OK; ++it) {
+      s = run_half(c, first);
+      if (s == NMF_OK) s = run_half(c, 1 - first);
+    }
+    cudaError_t le = cudaSuccess;
+    if (s == NMF_OK)
+      le = launch_objective(c->V, c->n, c->W, c->H, c->p, c->n, c->r, c->obj_parts,
+                            objective_parts(), c->f_dev, c->st);
+    if (s == NMF_OK && le == cudaSuccess) le = launch_run_test(c->run_dev, c->f_dev, k, loop, c->st);
+    c->capturing = false;
+    c->st = user;
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(c->cap_st, &out);
+    if (e == cudaSuccess) e = le;
+  }
+  if (e == cudaSuccess && s == NMF_OK) e = cudaGraphInstantiate(&c->conv_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (s != NMF_OK) return s;
+  if (e != cudaSuccess) {
+    c->conv_exec = nullptr;
+    return cuda_fail(c, e, "convergence graph");
+  }
+  c->conv_k = k;
+  return NMF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nmf_status nmf_converge(nmf_ctx* c, int max_iters, double tol, int check_every,
+                        int* iters_done, double* f_out) {
+  if (!c) { set_err(nullptr, "ctx is NULL"); return NMF_EINVAL; }
+  if (max_iters < 0 || check_every < 1 || !(tol >= 0.0)) {
+    set_err(&c->err, "need max_iters >= 0, check_every >= 1, tol >= 0");
+    return NMF_EINVAL;
+  }
+  nmf_status s = NMF_OK;
+  const bool loop = max_iters >= check_every;
+  if (loop && (s = build_conv_graph(c, check_every)) != NMF_OK) return s;
+  {
+    ProfScope ps(c, 2);
+    CK(launch_objective(c->V, c->n, c->W, c->H, c->p, c->n, c->r, c->obj_parts,
+                        objective_parts(), c->f_dev, c->st), "objective");
+    launched(2);
+  }
+  CK(launch_run_init(c->run_dev, c->f_dev, max_iters, tol, c->st), "run init");
+  launched(1);
+  if (loop) CK(cudaGraphLaunch(c->conv_exec, c->st), "graph launch");
+  CK(cudaMemcpyAsync(c->run_host, c->run_dev, sizeof(RunState), cudaMemcpyDeviceToHost, c->st),
+     "memcpy run state");
+  if ((s = check_device_error(c)) != NMF_OK) return s;
+  const RunState r = *c->run_host;
+  // kernels the graph ran: two per iteration, three per test
+  launched(2 * r.done + 3 * r.checks);
+  int done = r.done;
+  double f = r.f;
+  if (!r.stop && done < max_iters) {
+    // the remaining iterations, fewer than check_every, and the final objective
+    if ((s = nmf_step(c, max_iters - done)) != NMF_OK) return s;
+    done = max_iters;
+    if ((s = nmf_objective(c, &f)) != NMF_OK) return s;
   }
   if (iters_done) *iters_done = done;
   if (f_out) *f_out = f;

@@ -41,8 +41,10 @@ struct TcGram {
   double* gpart;                 // workspace, grid * r * r doubles
   float* Gpad;                   // out: rpad x rpad float32 (zero padded)
   double* G64;                   // out: r x r float64
-  unsigned long long* ctr;       // monotone counter
-  unsigned long long base;       // value before this launch (advances by 2 x grid)
+  unsigned long long* ctr;       // monotone counter, starts at 0
+  unsigned long long unit;       // every launch adds 2 x unit; unit >= grid of every
+                                 // launch on this counter (fixed for its lifetime)
+  unsigned long long skew;       // added to the wait targets: 0 (test hook)
 };
 
 nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, const void* Y_hi,

@@ -45,7 +45,7 @@ EXPORTS = [
     "nmf_batched_step", "nmf_batched_objective", "nmf_batched_destroy",
     "nmf_status_str", "nmf_last_error", "nmf_version", "nmf_restart",
     "nmf_kernel_launches", "nmf_profile_enable", "nmf_profile_read", "nmf_gram_noalloc",
-    "nmf_selfcheck_div", "nmf_test_expire_next_wait",
+    "nmf_selfcheck_div", "nmf_test_expire_next_wait", "nmf_converge",
 ]
 
 _lib = None
@@ -71,6 +71,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "nmf_objective": ([c_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "nmf_run": ([c_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "nmf_converge": ([c_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)],
+                         ctypes.c_int),
         "nmf_read_gram": ([c_p, ctypes.c_int, c_p], ctypes.c_int),
         "nmf_solve": ([cfgp, c_p, c_p, c_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), c_p],
                       ctypes.c_int),
@@ -195,6 +198,14 @@ class NMF:
         done, f = ctypes.c_int(), ctypes.c_double()
         _check(self.lib.nmf_run(self.ctx, int(max_iters), float(tol), int(check_every),
                                 ctypes.byref(done), ctypes.byref(f)), self.ctx)
+        return done.value, f.value
+
+    def converge(self, max_iters: int, tol: float = 1e-9, check_every: int = 1):
+        """run() with the loop on the device (one CUDA graph with a while-node;
+        the stopping test sets its condition).  Same results as run()."""
+        done, f = ctypes.c_int(), ctypes.c_double()
+        _check(self.lib.nmf_converge(self.ctx, int(max_iters), float(tol), int(check_every),
+                                     ctypes.byref(done), ctypes.byref(f)), self.ctx)
         return done.value, f.value
 
     def expire_next_wait(self):
