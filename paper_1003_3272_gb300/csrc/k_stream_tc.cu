@@ -458,8 +458,9 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
       // order, and the update of each entry from old, num and den
       tcepi::cluster_update<RPAD, kThreads>(S, Acc, Ns, Os, Ds, a.ep, q, row0, rows);
     }
-    cluster.sync();   // peers are done reading this block's tile; Ns is complete
-    if (!*(volatile int*)&s_abort) tcepi::store_cols<RPAD, kThreads>(Ns, a.ep, row0, rows);
+    __syncthreads();  // Ns is complete
+    if (!abort) tcepi::store_cols<RPAD, kThreads>(Ns, a.ep, row0, rows);
+    cluster.sync();   // peers are done reading this block's tile
     // The next tile's copies overwrite this shared memory through the async proxy.
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();

@@ -23,6 +23,7 @@
 #include <type_traits>
 
 #include "epilogue.cuh"
+#include "tc_ptx.cuh"
 
 namespace nmf {
 namespace tcepi {
@@ -169,7 +170,6 @@ __device__ void cluster_update_s(const float* Acc, float* Ns, const float* Os, c
   constexpr int LO = ldo<RPAD>();
   constexpr int LD = ldd<RPAD>();
   const int r = e.r;
-  cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
 #pragma unroll 1
   for (int j0 = 0; j0 < J; j0 += JC) {
     float4 v[JC][S];
@@ -178,9 +178,14 @@ __device__ void cluster_update_s(const float* Acc, float* Ns, const float* Os, c
       const int i = threadIdx.x + (j0 + j) * NT;
       if (j0 + j < J && i < TOT) {
         const int m = i / NQ, k4 = (i - m * NQ) * 4;
-        const float4* mine = reinterpret_cast<const float4*>(&Acc[(q * R + m) * LDA + k4]);
+        const float* mine = &Acc[(q * R + m) * LDA + k4];
+        const uint32_t sa = ptx::smem_u32(mine);
+        // this block's own partial from its shared memory, the peers' over
+        // distributed shared memory
 #pragma unroll
-        for (int s = 0; s < S; ++s) v[j][s] = *cluster.map_shared_rank(mine, s);
+        for (int s = 0; s < S; ++s)
+          v[j][s] = s == q ? *reinterpret_cast<const float4*>(mine)
+                           : ptx::ld_dsmem_v4(ptx::mapa(sa, (uint32_t)s));
       }
     }
 #pragma unroll
