@@ -13,7 +13,11 @@ The headline line is the split-BF16x3 tensor-core form (the form that meets
 the 1e-5 relative objective bar); `by_precision` reports the plain FP32 form
 and TF32 / BF16 on the same workload, `batched` the 512-instance batched
 workload (grouped persistent launches), `accuracy` each form's objective
-error against the FP64 oracle.
+error against the FP64 oracle, `converge` Section 3's protocol (iterate to a
+relative objective change below 1e-9, testing every iteration) on the
+CBCL-shaped 361 x 2429, r = 10 workload with the loop on the host and on
+the device (one CUDA graph), `poisson` the paper's Poisson variant (the
+simultaneous square-root update) on an 8192 x 8192, r = 50 counts matrix.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU
 oracle instead (the reference arm), on a bounded sample of the same workload.
@@ -364,6 +368,96 @@ def time_batched(prec, steps, warmup, iters, ws):
     return out
 
 
+def time_poisson(ws, clocks, steps=3, iters=10):
+    """The Poisson model of Section 3.1 (simultaneous square-root MM update)
+    on the counts workload (8192 x 8192 counts ~ Poisson(W* H*), mean 5,
+    r = 50): iterations/s through nmf_step with the inputs resident, each
+    iteration 8pnr flops on the float32 FMA pipes (b = WH formed once per
+    pass, two passes), against the FFMA peak at the sampled clock."""
+    import torch
+    from paper_1003_3272_gb300 import nmf, synth
+    pr = synth.counts()
+    p, n, r = pr.p, pr.n, pr.r
+    V = torch.from_numpy(pr.V).cuda()
+    W = torch.from_numpy(pr.W0).cuda()
+    H = torch.from_numpy(pr.H0).cuda()
+    stream = torch.cuda.current_stream()
+    with nmf.NMF(V, W, H, eps=pr.eps, model="poisson", seed=pr.seed, stream=stream) as m:
+        L0 = m.objective()
+        m.step(2)
+        torch.cuda.synchronize()
+        m.profile(True)
+        barrier(ws)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            m.step(iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), ws)
+        it_ms, it_n = m.profile_read(0)
+        m.profile(False)
+        L1 = m.objective()
+    done = steps * iters
+    flops = 8.0 * p * n * r
+    per_it = it_ms / max(1, it_n)
+    pk = peaks()
+    mhz = (clocks or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    peak = SMS * FFMA_PER_SM_PER_CLK * 2 * mhz * 1e6 / 1e12
+    achieved = flops / (per_it * 1e-3) / 1e12
+    del V, W, H
+    torch.cuda.empty_cache()
+    return {"workload": synth.COUNTS["name"] + " (counts ~ Poisson(W* H*), mean 5)",
+            "model": "poisson", "precision": "fp32", "iterations": done,
+            "value": round(job_rate(done, ms / 1e3, ws), 1), "unit": "iterations/s",
+            "ms_per_iteration": round(per_it, 4),
+            "roofline": {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1),
+                         "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                         "peak_source": "152 SMs x 128 FFMA x 2 x sampled SM clock",
+                         "flops_per_iteration": flops},
+            "loglik_start": L0, "loglik_end": L1}
+
+
+def time_converge(ws, prec="fp32", tol=1e-9, max_iters=100000):
+    """Section 3's protocol on the CBCL-shaped workload (faces 361 x 2429,
+    r = 10): iterate until the relative objective change drops below tol
+    (1e-9) or max_iters (1e5), testing after every iteration, once with the
+    loop on the host (nmf_run: one synchronisation per test) and once on the
+    device (nmf_converge: one CUDA graph, one synchronisation)."""
+    import numpy as np
+    import torch
+    from paper_1003_3272_gb300 import nmf, synth
+    pr = synth.faces()
+    res = {}
+    finals = {}
+    for method in ("converge", "run"):
+        V = torch.from_numpy(pr.V).cuda()
+        W = torch.from_numpy(pr.W0).cuda()
+        H = torch.from_numpy(pr.H0).cuda()
+        with nmf.NMF(V, W, H, eps=pr.eps, prec=prec) as m:
+            t0 = time.perf_counter()
+            getattr(m, method)(1, tol=tol, check_every=1)    # builds the graph (converge)
+            tb = time.perf_counter() - t0
+            m.restart(synth.BASE_SEED)                       # a fresh seeded start
+            torch.cuda.synchronize()
+            barrier(ws)
+            t0 = time.perf_counter()
+            done, f = getattr(m, method)(max_iters, tol=tol, check_every=1)
+            te = max_over_ranks(time.perf_counter() - t0, ws)
+            finals[method] = (done, f, W.cpu().numpy(), H.cpu().numpy())
+        res[method] = {"iterations": done, "seconds": round(te, 4),
+                       "iters_per_s": round(done * ws / te, 1), "objective": f,
+                       "first_call_ms": round(tb * 1e3, 2)}
+    a, b = finals["converge"], finals["run"]
+    return {"workload": "faces_361x2429_r10 (seeded start from nmf_restart)",
+            "precision": prec, "tol": tol, "max_iters": max_iters, "check_every": 1,
+            "device_loop": res["converge"], "host_loop": res["run"],
+            "device_over_host": round(res["run"]["seconds"] / res["converge"]["seconds"], 3),
+            "identical_results": bool(a[0] == b[0] and a[1] == b[1]
+                                      and np.array_equal(a[2], b[2])
+                                      and np.array_equal(a[3], b[3]))}
+
+
 def oracle_objective(workload, iters):
     """The float64 oracle's objective after `iters` iterations from the seeded
     start on `workload`, as stored in tests/golden/objectives.json (written by
@@ -501,6 +595,8 @@ def run_gpu(args, ws, rank, local):
         out["accuracy"] = accuracy(wname, iters, objs)
         if args.workload == "planted":
             out["batched"] = time_batched("bf16x3", max(2, args.steps // 2), 2, 20, ws)
+            out["converge"] = time_converge(ws)
+            out["poisson"] = time_poisson(ws, clocks)
     else:
         out["accuracy"] = accuracy(wname, iters, {args.prec: main["objective"]})
     return out, pr

@@ -73,6 +73,24 @@ typedef enum {
   NMF_ORDER_W_FIRST = 1  /* W then H: Algorithm 1's order                   */
 } nmf_order;
 
+/* The model the factors are fitted under (Section 3.1).
+ *   NMF_MODEL_GAUSSIAN : minimise ||V - W H||_F^2 by Algorithm 1 (the
+ *                        alternating updates above); every precision.
+ *   NMF_MODEL_POISSON  : maximise the Poisson loglikelihood
+ *                        L = sum_ij [v_ij ln (WH)_ij - (WH)_ij] by the
+ *                        paper's simultaneous square-root MM update
+ *                          W_ik <- W_ik sqrt((sum_j v_ij H_kj / b_ij) / sum_j H_kj)
+ *                          H_kj <- H_kj sqrt((sum_i v_ij W_ik / b_ij) / sum_i W_ik)
+ *                        with b = W H from the same iteration (eps guards
+ *                        the divisions; a term with v_ij = 0 is zero).
+ *                        NMF_FP32 and r <= 64 only (else NMF_EUNSUPPORTED);
+ *                        `order` is ignored; nmf_objective returns L;
+ *                        nmf_half_step and nmf_read_gram are not served.  */
+typedef enum {
+  NMF_MODEL_GAUSSIAN = 0,
+  NMF_MODEL_POISSON = 1
+} nmf_model;
+
 typedef struct {
   int64_t p;             /* rows of V and W                                 */
   int64_t n;             /* columns of V and H                              */
@@ -88,7 +106,7 @@ typedef struct {
                             non-finite entry (NMF_ENONFINITE)               */
   int32_t split_k;       /* 0: automatic; otherwise the number of K-splits
                             per output tile of each product (tuning knob)   */
-  int32_t reserved;
+  int32_t model;         /* nmf_model (0: Gaussian, the default)           */
 } nmf_config;
 
 typedef struct nmf_ctx nmf_ctx;

@@ -1,0 +1,381 @@
+// Poisson variant of the MM NMF iteration (Section 3.1, closing paragraph):
+// maximise L = sum_ij [v_ij ln b_ij - b_ij], b = W H, by the simultaneous
+// square-root update the paper prints after it,
+//     w_ik <- w_ik sqrt( (sum_j v_ij h_kj / b_ij) / (sum_j h_kj) )
+//     h_kj <- h_kj sqrt( (sum_i v_ij w_ik / b_ij) / (sum_i w_ik) )
+// with b, the sums and both right-hand sides from the factors of the same
+// iteration.  eps guards the two divisions (v / (b + eps), num / (den + eps));
+// a term with v_ij = 0 is zero.
+//
+// One iteration is four launches on the float32 FMA pipes:
+//   k_pois_sums    the r row sums of H and column sums of W (float64, a
+//                  fixed-order tree per rank);
+//   k_pois_pass<0> per 64-row panel of V and a segment of its 64-column
+//                  tiles: b = W_I H_J (K = r), q = v / (b + eps), and the
+//                  numerator of W, q H_J^T (K = 64), summed over the
+//                  segment's tiles (float32 within a tile, compensated
+//                  two-sum across tiles, written out in float64);
+//   k_pois_pass<1> the same per 64-column panel and a segment of its row
+//                  tiles, with the numerator of H, W_I^T q;
+//   k_pois_update  both factors in place from the segment partials (summed
+//                  in segment order), the sums and the old factors.
+// Both passes read V once each (float32, row-major, as the caller holds it);
+// b is formed twice (once per pass), so an iteration is 8pnr flops.  Every
+// sum runs in a fixed order: the result is deterministic.
+#include <cstdint>
+
+#include "nmf_internal.cuh"
+
+namespace nmf {
+namespace {
+
+constexpr int kPT = 64;          // tile edge (rows and columns of V)
+constexpr int kPThreads = 256;   // 16 x 16 threads, a 4 x 4 sub-tile each
+constexpr int kPMaxRank = 64;
+
+struct PoisShape {
+  int r, r4;                     // rank, rank rounded up to 4
+  int lgop;                      // row stride of the GEMM2 operand tile
+  __device__ __host__ int wt() const { return 0; }                     // [r][64]
+  __device__ __host__ int hs() const { return r * kPT; }               // [r][64]
+  __device__ __host__ int gop() const { return 2 * r * kPT; }          // [64][lgop]
+  __device__ __host__ int qs() const { return 2 * r * kPT + kPT * lgop; }  // [64][68]
+  __device__ __host__ int floats() const { return qs() + kPT * (kPT + 4); }
+};
+
+__host__ __device__ inline PoisShape pois_shape(int r) {
+  PoisShape s;
+  s.r = r;
+  s.r4 = (r + 3) & ~3;
+  s.lgop = s.r4 + 4;
+  return s;
+}
+
+// Row sums of H (which = 0: den of the W update) or column sums of W
+// (which = 1: den of the H update) for rank k = blockIdx.x / 2 ... in float64.
+__global__ void k_pois_sums(const float* __restrict__ W, const float* __restrict__ H,
+                            int64_t p, int64_t n, int r, double* __restrict__ sums) {
+  __shared__ double red[kPThreads];
+  const int k = blockIdx.x >> 1, which = blockIdx.x & 1;
+  double s = 0.0;
+  if (which == 0) {
+    for (int64_t j = threadIdx.x; j < n; j += kPThreads) s += (double)H[(int64_t)k * n + j];
+  } else {
+    for (int64_t i = threadIdx.x; i < p; i += kPThreads) s += (double)W[i * r + k];
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kPThreads / 2; w >= 1; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sums[which * r + k] = red[0];
+}
+
+// Loads a 64 x 64 tile of V (rows i0.., columns j0..) for the thread's 4 x 4
+// sub-tile: rows i0 + 4 ty + a, columns j0 + 4 tx + c; zero outside V.
+__device__ __forceinline__ void load_v(const float* __restrict__ V, int64_t ldv, int64_t p,
+                                       int64_t n, int64_t i0, int64_t j0, int ty, int tx,
+                                       bool vec, float (&v)[4][4]) {
+  const int64_t jc = j0 + 4 * tx;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t i = i0 + 4 * ty + a;
+    if (i < p && vec && jc + 3 < n) {
+      const float4 x = __ldcs(reinterpret_cast<const float4*>(V + i * ldv + jc));
+      v[a][0] = x.x; v[a][1] = x.y; v[a][2] = x.z; v[a][3] = x.w;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        v[a][c] = (i < p && jc + c < n) ? __ldcs(V + i * ldv + jc + c) : 0.f;
+    }
+  }
+}
+
+// Stages W rows [i0, i0 + 64) as Wt[k][i] (GEMM1) and, when gop != nullptr,
+// as gop[i][k] (GEMM2); H columns [j0, j0 + 64) as Hs[k][j] and gop[j][k].
+// Zero outside the factors and for ranks r .. r4-1 of gop.  Each layout has
+// its own loop, with consecutive threads on consecutive shared-memory words
+// (the transposing reads hit the L1 copy of the same small block).
+__device__ __forceinline__ void stage_w(const float* __restrict__ W, int64_t p, int r, int r4,
+                                        int lgop, int64_t i0, float* Wt, float* gop) {
+  for (int idx = threadIdx.x; idx < r * kPT; idx += kPThreads) {
+    const int k = idx / kPT, i = idx - k * kPT;
+    Wt[idx] = i0 + i < p ? W[(i0 + i) * r + k] : 0.f;
+  }
+  if (gop)
+    for (int idx = threadIdx.x; idx < kPT * r4; idx += kPThreads) {
+      const int i = idx / r4, k = idx - i * r4;
+      gop[i * lgop + k] = (k < r && i0 + i < p) ? W[(i0 + i) * r + k] : 0.f;
+    }
+}
+__device__ __forceinline__ void stage_h(const float* __restrict__ H, int64_t n, int r, int r4,
+                                        int lgop, int64_t j0, float* Hs, float* gop) {
+  for (int idx = threadIdx.x; idx < r * kPT; idx += kPThreads) {
+    const int k = idx / kPT, j = idx - k * kPT;
+    Hs[idx] = j0 + j < n ? H[(int64_t)k * n + j0 + j] : 0.f;
+  }
+  if (gop)
+    for (int idx = threadIdx.x; idx < kPT * r4; idx += kPThreads) {
+      const int j = idx / r4, k = idx - j * r4;
+      gop[j * lgop + k] = (k < r && j0 + j < n) ? H[(int64_t)k * n + j0 + j] : 0.f;
+    }
+}
+
+// Knuth's two-sum: s + e = a + b exactly (round to nearest).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// MODE 0: block = (row panel I, segment of column tiles); numerator of W.
+// MODE 1: block = (column panel J, segment of row tiles); numerator of H.
+// part: MODE 0 [seg][p][r], MODE 1 [seg][n][r] (float64).  Ranks above 64
+// are not served (pois_supported).
+template <int MODE>
+__global__ void __launch_bounds__(kPThreads)
+k_pois_pass(const float* __restrict__ V, int64_t ldv, const float* __restrict__ W,
+            const float* __restrict__ H, int64_t p, int64_t n, int r, float eps, int segs,
+            double* __restrict__ part) {
+  extern __shared__ float sm[];
+  const PoisShape sh = pois_shape(r);
+  float* Wt = sm + sh.wt();
+  float* Hs = sm + sh.hs();
+  float* Gop = sm + sh.gop();
+  float* Qs = sm + sh.qs();
+  constexpr int LQ = kPT + 4;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int panel = blockIdx.x / segs, seg = blockIdx.x - panel * segs;
+  const int64_t panel0 = (int64_t)panel * kPT;
+  const int64_t other = MODE == 0 ? n : p;              // extent streamed
+  const int ntiles = (int)((other + kPT - 1) / kPT);
+  const int t0 = (int)((int64_t)seg * ntiles / segs);
+  const int t1 = (int)((int64_t)(seg + 1) * ntiles / segs);
+  const bool vec = (ldv % 4 == 0) && (reinterpret_cast<uintptr_t>(V) % 16 == 0);
+  // GEMM2 item of this thread: rows (MODE 0) or columns (MODE 1) 4 g .. 4 g + 3
+  // of the panel, ranks 4 c .. 4 c + 3
+  const int g = tid & 15, c = tid >> 4;
+  const bool item = 4 * c < sh.r4;
+
+  // the panel's resident factor block
+  if (MODE == 0) stage_w(W, p, r, sh.r4, sh.lgop, panel0, Wt, nullptr);
+  else stage_h(H, n, r, sh.r4, sh.lgop, panel0, Hs, nullptr);
+
+  // the segment's running sums, compensated across tiles: hi + lo
+  float tot[4][4], err[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) tot[a][b] = err[a][b] = 0.f;
+
+  for (int t = t0; t < t1; ++t) {
+    const int64_t o0 = (int64_t)t * kPT;
+    const int64_t i0 = MODE == 0 ? panel0 : o0;
+    const int64_t j0 = MODE == 0 ? o0 : panel0;
+    float v[4][4];
+    load_v(V, ldv, p, n, i0, j0, ty, tx, vec, v);
+    __syncthreads();   // the previous tile's operands are consumed
+    if (MODE == 0) stage_h(H, n, r, sh.r4, sh.lgop, j0, Hs, Gop);
+    else stage_w(W, p, r, sh.r4, sh.lgop, i0, Wt, Gop);
+    __syncthreads();
+
+    // GEMM1: b = W_I H_J for rows 4 ty.., columns 4 tx..
+    float b[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) b[a][e] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < r; ++k) {
+      const float4 w4 = *reinterpret_cast<const float4*>(&Wt[k * kPT + 4 * ty]);
+      const float4 h4 = *reinterpret_cast<const float4*>(&Hs[k * kPT + 4 * tx]);
+      const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+      const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) b[a][e] = fmaf(wv[a], hv[e], b[a][e]);
+    }
+    // q = v / (b + eps); zero where v is zero.  MODE 0 stores Q^T [j][i],
+    // MODE 1 stores Q [i][j].
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float q = v[a][e] == 0.f ? 0.f : div_rn(v[a][e], __fadd_rn(b[a][e], eps));
+        if (MODE == 0) Qs[(4 * tx + e) * LQ + 4 * ty + a] = q;
+        else Qs[(4 * ty + a) * LQ + 4 * tx + e] = q;
+      }
+    __syncthreads();
+
+    // GEMM2 over the tile's 64 entries of K (columns for MODE 0, rows for
+    // MODE 1): acc[x][y] for rows/columns 4 g + x and ranks 4 c + y.
+    if (item) {
+      float acc[4][4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+#pragma unroll 4
+      for (int kk = 0; kk < kPT; ++kk) {
+        const float4 q4 = *reinterpret_cast<const float4*>(&Qs[kk * LQ + 4 * g]);
+        const float4 f4 = *reinterpret_cast<const float4*>(&Gop[kk * sh.lgop + 4 * c]);
+        const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
+        const float fv[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(qv[x], fv[y], acc[x][y]);
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          float e;
+          two_sum(tot[x][y], acc[x][y], tot[x][y], e);
+          err[x][y] = __fadd_rn(err[x][y], e);
+        }
+    }
+  }
+
+  if (item) {
+    const int64_t extent = MODE == 0 ? p : n;
+    double* dst = part + (int64_t)seg * extent * r;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const int64_t m = panel0 + 4 * g + x;
+      if (m >= extent) continue;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int k = 4 * c + y;
+        if (k < r) dst[m * r + k] = (double)tot[x][y] + (double)err[x][y];
+      }
+    }
+  }
+}
+
+// Both factors in place: W entries (idx < p r) and H entries (the rest).
+__global__ void k_pois_update(float* __restrict__ W, float* __restrict__ H, int64_t p,
+                              int64_t n, int r, float eps, const double* __restrict__ partW,
+                              int segW, const double* __restrict__ partH, int segH,
+                              const double* __restrict__ sums) {
+  const int64_t nw = p * r, total = nw + (int64_t)r * n;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    if (idx < nw) {
+      const int64_t i = idx / r;
+      const int k = (int)(idx - i * r);
+      double num = 0.0;
+      for (int s = 0; s < segW; ++s) num += partW[((int64_t)s * p + i) * r + k];
+      const double ratio = num / (sums[k] + (double)eps);
+      W[idx] = (float)((double)W[idx] * sqrt(ratio));
+    } else {
+      const int64_t h = idx - nw;
+      const int k = (int)(h / n);
+      const int64_t j = h - (int64_t)k * n;
+      double num = 0.0;
+      for (int s = 0; s < segH; ++s) num += partH[((int64_t)s * n + j) * r + k];
+      const double ratio = num / (sums[r + k] + (double)eps);
+      H[h] = (float)((double)H[h] * sqrt(ratio));
+    }
+  }
+}
+
+// L = sum_ij [v_ij ln b_ij - b_ij] in float64 (b formed in float64), per
+// block partials in a fixed order; 0 ln 0 = 0.
+constexpr int kLBlocks = 1216;
+__global__ void __launch_bounds__(kPThreads)
+k_pois_loglik(const float* __restrict__ V, int64_t ldv, const float* __restrict__ W,
+              const float* __restrict__ H, int64_t p, int64_t n, int r,
+              double* __restrict__ partials) {
+  __shared__ double red[kPThreads];
+  double s = 0.0;
+  const int64_t total = p * n;
+  for (int64_t idx = (int64_t)blockIdx.x * kPThreads + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * kPThreads) {
+    const int64_t i = idx / n, j = idx - i * n;
+    double b = 0.0;
+    for (int k = 0; k < r; ++k) b = fma((double)W[i * r + k], (double)H[(int64_t)k * n + j], b);
+    const double v = (double)V[i * ldv + j];
+    s += (v != 0.0 ? v * log(b) : 0.0) - b;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kPThreads / 2; w >= 1; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+__global__ void k_pois_sum(const double* __restrict__ partials, int nparts,
+                           double* __restrict__ out) {
+  __shared__ double red[kPThreads];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += kPThreads) s += partials[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kPThreads / 2; w >= 1; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+}  // namespace
+
+bool pois_supported(int r) { return r >= 1 && r <= kPMaxRank; }
+
+static size_t pois_smem_bytes(int r) { return (size_t)pois_shape(r).floats() * sizeof(float); }
+
+PoisPlan pois_plan(int64_t p, int64_t n, int r, int sms) {
+  PoisPlan pl;
+  const int64_t tp = (p + kPT - 1) / kPT, tn = (n + kPT - 1) / kPT;
+  // about four resident blocks per SM in each pass
+  const int64_t target = 4 * (int64_t)sms;
+  auto segs = [&](int64_t panels, int64_t tiles) {
+    int64_t s = (target + panels - 1) / panels;
+    if (s > tiles) s = tiles;
+    if (s < 1) s = 1;
+    return (int)s;
+  };
+  pl.segW = segs(tp, tn);
+  pl.segH = segs(tn, tp);
+  pl.gridW = (int)(tp * pl.segW);
+  pl.gridH = (int)(tn * pl.segH);
+  pl.smem = (int)pois_smem_bytes(r);
+  return pl;
+}
+
+int pois_loglik_parts() { return kLBlocks; }
+
+cudaError_t pois_iteration(const PoisPlan& pl, const float* V, int64_t ldv, float* W, float* H,
+                           int64_t p, int64_t n, int r, float eps, double* sums, double* partW,
+                           double* partH, cudaStream_t st) {
+  cudaError_t e;
+  e = cudaFuncSetAttribute(k_pois_pass<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_pois_pass<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
+  if (e != cudaSuccess) return e;
+  k_pois_sums<<<2 * r, kPThreads, 0, st>>>(W, H, p, n, r, sums);
+  k_pois_pass<0><<<pl.gridW, kPThreads, pl.smem, st>>>(V, ldv, W, H, p, n, r, eps, pl.segW,
+                                                        partW);
+  k_pois_pass<1><<<pl.gridH, kPThreads, pl.smem, st>>>(V, ldv, W, H, p, n, r, eps, pl.segH,
+                                                        partH);
+  const int64_t total = p * r + (int64_t)r * n;
+  int64_t blocks = (total + kPThreads - 1) / kPThreads;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_pois_update<<<(unsigned)blocks, kPThreads, 0, st>>>(W, H, p, n, r, eps, partW, pl.segW,
+                                                         partH, pl.segH, sums);
+  return cudaGetLastError();
+}
+
+cudaError_t pois_loglik(const float* V, int64_t ldv, const float* W, const float* H, int64_t p,
+                        int64_t n, int r, double* partials, double* out, cudaStream_t st) {
+  k_pois_loglik<<<kLBlocks, kPThreads, 0, st>>>(V, ldv, W, H, p, n, r, partials);
+  k_pois_sum<<<1, kPThreads, 0, st>>>(partials, kLBlocks, out);
+  return cudaGetLastError();
+}
+
+}  // namespace nmf

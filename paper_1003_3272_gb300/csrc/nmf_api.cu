@@ -106,6 +106,13 @@ struct nmf_ctx {
   bool prof = false;
   bool in_step = false;       // inside nmf_step (tensor-core launches timed as a group)
   bool capturing = false;     // recording the convergence graph: no events, no test skew
+  // Poisson model: plan and workspaces (k_poisson.cu)
+  bool pois = false;
+  PoisPlan pplan{};
+  double* psums = nullptr;        // 2r: row sums of H, column sums of W
+  double* ppartW = nullptr;       // segW x p x r
+  double* ppartH = nullptr;       // segH x n x r
+  double* pobj_parts = nullptr;   // loglikelihood partials
   // nmf_converge: the run's device state and the graph of its loop, built
   // for one check interval and kept until another is asked for
   RunState* run_dev = nullptr;
@@ -213,6 +220,14 @@ nmf_status validate_cfg(const nmf_config* cfg) {
     return NMF_EINVAL;
   }
   if (cfg->split_k < 0) { set_err(nullptr, "split_k must be >= 0"); return NMF_EINVAL; }
+  if (cfg->model != NMF_MODEL_GAUSSIAN && cfg->model != NMF_MODEL_POISSON) {
+    set_err(nullptr, "unknown model");
+    return NMF_EINVAL;
+  }
+  if (cfg->model == NMF_MODEL_POISSON && (cfg->prec != NMF_FP32 || !pois_supported(cfg->r))) {
+    set_err(nullptr, "the Poisson model is served in NMF_FP32 for ranks 1..64");
+    return NMF_EUNSUPPORTED;
+  }
   if (cfg->p > (int64_t)1 << 31 || cfg->n > (int64_t)1 << 31) {
     set_err(nullptr, "p and n must be <= 2^31");
     return NMF_EINVAL;
@@ -227,6 +242,14 @@ nmf_status prepare(nmf_ctx* c, bool seed_factors, uint64_t seed) {
   const int r = c->r;
   cudaStream_t st = c->st;
   ProfScope ps(c, 3);
+  if (c->pois) {
+    if (seed_factors) {
+      CK(launch_seed_uniform(c->W, p * r, seed, 1, st), "seed W");
+      CK(launch_seed_uniform(c->H, (int64_t)r * n, seed, 2, st), "seed H");
+      launched(2);
+    }
+    return NMF_OK;
+  }
   {
     // tile-blocked copies: Xw = V (p x n), Xh = V^T (n x p)
     const int mode = c->plane == kPlaneTF32 ? 1 : (c->plane == kPlaneF32 ? 2 : 0);
@@ -254,6 +277,33 @@ nmf_status prepare(nmf_ctx* c, bool seed_factors, uint64_t seed) {
   CK(launch_gram_reduce(c->gpart[1], c->gcount[1], r, c->GH32, c->GH64, st), "gram H reduce");
   launched(6);
   return NMF_OK;
+}
+
+// The objective value, the error word and the run state (both models).
+nmf_status alloc_common(nmf_ctx* c) {
+  nmf_status s;
+  if ((s = dalloc(c, (void**)&c->f_dev, 8)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->err_dev, sizeof(int))) != NMF_OK) return s;
+  CK(cudaMallocHost((void**)&c->f_host, 8), "cudaMallocHost");
+  CK(cudaMallocHost((void**)&c->err_host, sizeof(int)), "cudaMallocHost");
+  if ((s = dalloc(c, (void**)&c->run_dev, sizeof(RunState))) != NMF_OK) return s;
+  CK(cudaMallocHost((void**)&c->run_host, sizeof(RunState)), "cudaMallocHost");
+  return NMF_OK;
+}
+
+// Poisson model: V is read as the caller holds it (no operand copies).
+nmf_status build_poisson(nmf_ctx* c) {
+  const int64_t p = c->p, n = c->n;
+  const int r = c->r;
+  nmf_status s;
+  c->pois = true;
+  c->pplan = pois_plan(p, n, r, c->sms);
+  if ((s = dalloc(c, (void**)&c->psums, 2 * (size_t)r * 8)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->ppartW, (size_t)c->pplan.segW * p * r * 8)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->ppartH, (size_t)c->pplan.segH * n * r * 8)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->pobj_parts, (size_t)pois_loglik_parts() * 8)) != NMF_OK) return s;
+  if ((s = alloc_common(c)) != NMF_OK) return s;
+  return prepare(c, c->cfg.init_from_seed != 0, c->cfg.seed);
 }
 
 nmf_status build_ctx(nmf_ctx* c) {
@@ -287,6 +337,7 @@ nmf_status build_ctx(nmf_ctx* c) {
       return NMF_ENONFINITE;
     }
   }
+  if (c->cfg.model == NMF_MODEL_POISSON) return build_poisson(c);
   // Operand copies of V.
   const bool bf = (prec == NMF_BF16X3 || prec == NMF_BF16);
   const int elem = bf ? 2 : 4;
@@ -371,13 +422,7 @@ nmf_status build_ctx(nmf_ctx* c) {
     if ((s = dalloc(c, (void**)&c->tc_gpart, grid * rr * 8)) != NMF_OK) return s;
   }
   if ((s = dalloc(c, (void**)&c->obj_parts, objective_parts() * 8)) != NMF_OK) return s;
-  if ((s = dalloc(c, (void**)&c->f_dev, 8)) != NMF_OK) return s;
-  if ((s = dalloc(c, (void**)&c->err_dev, sizeof(int))) != NMF_OK) return s;
-  CK(cudaMallocHost((void**)&c->f_host, 8), "cudaMallocHost");
-  CK(cudaMallocHost((void**)&c->err_host, sizeof(int)), "cudaMallocHost");
-  if ((s = dalloc(c, (void**)&c->run_dev, sizeof(RunState))) != NMF_OK) return s;
-  CK(cudaMallocHost((void**)&c->run_host, sizeof(RunState)), "cudaMallocHost");
-
+  if ((s = alloc_common(c)) != NMF_OK) return s;
   return prepare(c, c->cfg.init_from_seed != 0, c->cfg.seed);
 }
 
@@ -442,6 +487,28 @@ nmf_status run_half(nmf_ctx* c, int which) {
   return NMF_OK;
 }
 
+// One full iteration of the context's model.
+nmf_status run_iteration(nmf_ctx* c) {
+  if (c->pois) {
+    CK(pois_iteration(c->pplan, c->V, c->n, c->W, c->H, c->p, c->n, c->r, c->cfg.eps, c->psums,
+                      c->ppartW, c->ppartH, c->st), "Poisson iteration");
+    if (!c->capturing) launched(4);
+    return NMF_OK;
+  }
+  const int first = c->cfg.order == NMF_ORDER_H_FIRST ? 0 : 1;
+  nmf_status s = run_half(c, first);
+  if (s == NMF_OK) s = run_half(c, 1 - first);
+  return s;
+}
+
+// The model's objective into f_dev (asynchronous): ||V - WH||_F^2 or L.
+cudaError_t launch_model_objective(nmf_ctx* c) {
+  if (c->pois)
+    return pois_loglik(c->V, c->n, c->W, c->H, c->p, c->n, c->r, c->pobj_parts, c->f_dev, c->st);
+  return launch_objective(c->V, c->n, c->W, c->H, c->p, c->n, c->r, c->obj_parts,
+                          objective_parts(), c->f_dev, c->st);
+}
+
 // Float64 Gram of factor f (0 = W, 1 = H), formed afresh from the factor.
 nmf_status reduce_gram(nmf_ctx* c, int f) {
   const int64_t M = f == 0 ? c->p : c->n;
@@ -495,22 +562,19 @@ nmf_status nmf_init(const nmf_config* cfg, const float* V, float* W, float* H, v
 nmf_status nmf_half_step(nmf_ctx* c, int which) {
   if (!c) { set_err(nullptr, "ctx is NULL"); return NMF_EINVAL; }
   if (which != 0 && which != 1) { set_err(&c->err, "which must be 0 (H) or 1 (W)"); return NMF_EINVAL; }
+  if (c->pois) { set_err(&c->err, "the Poisson update is simultaneous: no half steps"); return NMF_EUNSUPPORTED; }
   return run_half(c, which);
 }
 
 nmf_status nmf_step(nmf_ctx* c, int iters) {
   if (!c) { set_err(nullptr, "ctx is NULL"); return NMF_EINVAL; }
   if (iters < 0) { set_err(&c->err, "iters must be >= 0"); return NMF_EINVAL; }
-  const int first = c->cfg.order == NMF_ORDER_H_FIRST ? 0 : 1;
-  const bool tc = true;
-  // the streaming launches chain by programmatic dependent launch: one bracket
-  ProfScope ps(c, 0, tc ? 2 * iters : 0);
-  c->in_step = tc;
+  // The streaming launches chain by programmatic dependent launch: one
+  // bracket (for the Poisson model, one unit per iteration).
+  ProfScope ps(c, 0, c->pois ? iters : 2 * iters);
+  c->in_step = true;
   nmf_status s = NMF_OK;
-  for (int it = 0; it < iters && s == NMF_OK; ++it) {
-    s = run_half(c, first);
-    if (s == NMF_OK) s = run_half(c, 1 - first);
-  }
+  for (int it = 0; it < iters && s == NMF_OK; ++it) s = run_iteration(c);
   c->in_step = false;
   return s;
 }
@@ -519,8 +583,7 @@ nmf_status nmf_objective(nmf_ctx* c, double* f_out) {
   if (!c || !f_out) { set_err(c ? &c->err : nullptr, "ctx and f_out must be non-NULL"); return NMF_EINVAL; }
   {
     ProfScope ps(c, 2);
-    CK(launch_objective(c->V, c->n, c->W, c->H, c->p, c->n, c->r, c->obj_parts,
-                        objective_parts(), c->f_dev, c->st), "objective");
+    CK(launch_model_objective(c), "objective");
     launched(2);
   }
   CK(cudaMemcpyAsync(c->f_host, c->f_dev, 8, cudaMemcpyDeviceToHost, c->st), "memcpy f");
@@ -587,15 +650,9 @@ nmf_status build_conv_graph(nmf_ctx* c, int k) {
     cudaStream_t user = c->st;
     c->st = c->cap_st;
     c->capturing = true;
-    const int first = c->cfg.order == NMF_ORDER_H_FIRST ? 0 : 1;
-    for (int it = 0; it < k && s == NMF_OK; ++it) {
-      s = run_half(c, first);
-      if (s == NMF_OK) s = run_half(c, 1 - first);
-    }
+    for (int it = 0; it < k && s == NMF_OK; ++it) s = run_iteration(c);
     cudaError_t le = cudaSuccess;
-    if (s == NMF_OK)
-      le = launch_objective(c->V, c->n, c->W, c->H, c->p, c->n, c->r, c->obj_parts,
-                            objective_parts(), c->f_dev, c->st);
+    if (s == NMF_OK) le = launch_model_objective(c);
     if (s == NMF_OK && le == cudaSuccess) le = launch_run_test(c->run_dev, c->f_dev, k, loop, c->st);
     c->capturing = false;
     c->st = user;
@@ -630,8 +687,7 @@ nmf_status nmf_converge(nmf_ctx* c, int max_iters, double tol, int check_every,
   if (loop && (s = build_conv_graph(c, check_every)) != NMF_OK) return s;
   {
     ProfScope ps(c, 2);
-    CK(launch_objective(c->V, c->n, c->W, c->H, c->p, c->n, c->r, c->obj_parts,
-                        objective_parts(), c->f_dev, c->st), "objective");
+    CK(launch_model_objective(c), "objective");
     launched(2);
   }
   CK(launch_run_init(c->run_dev, c->f_dev, max_iters, tol, c->st), "run init");
@@ -641,8 +697,8 @@ nmf_status nmf_converge(nmf_ctx* c, int max_iters, double tol, int check_every,
      "memcpy run state");
   if ((s = check_device_error(c)) != NMF_OK) return s;
   const RunState r = *c->run_host;
-  // kernels the graph ran: two per iteration, three per test
-  launched(2 * r.done + 3 * r.checks);
+  // kernels the graph ran: two (Poisson: four) per iteration, three per test
+  launched((c->pois ? 4 : 2) * r.done + 3 * r.checks);
   int done = r.done;
   double f = r.f;
   if (!r.stop && done < max_iters) {
@@ -661,6 +717,7 @@ nmf_status nmf_read_gram(nmf_ctx* c, int which, double* out) {
     set_err(c ? &c->err : nullptr, "bad argument to nmf_read_gram");
     return NMF_EINVAL;
   }
+  if (c->pois) { set_err(&c->err, "the Poisson model forms no Gram matrices"); return NMF_EUNSUPPORTED; }
   nmf_status s = reduce_gram(c, which);
   if (s != NMF_OK) return s;
   CK(cudaMemcpyAsync(out, which == 0 ? c->GW64 : c->GH64, (size_t)c->r * c->r * 8,
@@ -719,6 +776,7 @@ nmf_status nmf_solve(const nmf_config* cfg, const float* V, float* W, float* H, 
 
 nmf_status nmf_test_expire_next_wait(nmf_ctx* c) {
   if (!c) { set_err(nullptr, "ctx is NULL"); return NMF_EINVAL; }
+  if (c->pois) { set_err(&c->err, "the Poisson kernels have no grid-wide waits"); return NMF_EUNSUPPORTED; }
   c->gctr_skew = 1ull << 40;   // a counter value no launch reaches
   return NMF_OK;
 }

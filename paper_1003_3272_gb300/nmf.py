@@ -21,6 +21,9 @@ PRECISIONS = {"fp32": FP32, "tf32": TF32, "bf16x3": BF16X3, "bf16": BF16}
 # nmf_order
 H_FIRST, W_FIRST = 0, 1
 ORDERS = {"h_first": H_FIRST, "w_first": W_FIRST}
+# nmf_model
+GAUSSIAN, POISSON = 0, 1
+MODELS = {"gaussian": GAUSSIAN, "poisson": POISSON}
 
 
 class Config(ctypes.Structure):
@@ -35,7 +38,7 @@ class Config(ctypes.Structure):
         ("init_from_seed", ctypes.c_int32),
         ("validate", ctypes.c_int32),
         ("split_k", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("model", ctypes.c_int32),
     ]
 
 
@@ -132,7 +135,7 @@ def _check(status: int, ctx=None):
 
 
 def make_config(p, n, r, eps=1e-10, prec="fp32", order="h_first", seed=0,
-                init_from_seed=False, validate=False, split_k=0) -> Config:
+                init_from_seed=False, validate=False, split_k=0, model="gaussian") -> Config:
     lib = load()
     cfg = Config()
     _check(lib.nmf_config_default(ctypes.byref(cfg), int(p), int(n), int(r)))
@@ -143,6 +146,7 @@ def make_config(p, n, r, eps=1e-10, prec="fp32", order="h_first", seed=0,
     cfg.init_from_seed = int(bool(init_from_seed))
     cfg.validate = int(bool(validate))
     cfg.split_k = int(split_k)
+    cfg.model = MODELS[model] if isinstance(model, str) else int(model)
     return cfg
 
 
@@ -163,7 +167,8 @@ class NMF:
     updated in place."""
 
     def __init__(self, V, W, H, eps=1e-10, prec="fp32", order="h_first", seed=0,
-                 init_from_seed=False, validate=False, split_k=0, stream=None):
+                 init_from_seed=False, validate=False, split_k=0, stream=None,
+                 model="gaussian"):
         import torch
         for name, t in (("V", V), ("W", W), ("H", H)):
             if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
@@ -177,7 +182,7 @@ class NMF:
         self.p, self.n, self.r = p, n, r
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.cfg = make_config(p, n, r, eps, prec, order, seed, init_from_seed, validate,
-                               split_k)
+                               split_k, model)
         ctx = ctypes.c_void_p()
         _check(self.lib.nmf_init(ctypes.byref(self.cfg), _ptr(V), _ptr(W), _ptr(H),
                                  _stream_handle(self.stream), ctypes.byref(ctx)))
@@ -254,7 +259,7 @@ class NMF:
 
 
 def solve(V, W, H, iters, eps=1e-10, prec="fp32", order="h_first", stream=None,
-          split_k=0) -> float:
+          split_k=0, model="gaussian") -> float:
     """One-call solve through ``nmf_solve``.  V, W, H are numpy float32 arrays
     (host; copied in and out inside the call, W and H overwritten) or CUDA
     tensors.  Returns the final objective."""
@@ -270,7 +275,7 @@ def solve(V, W, H, iters, eps=1e-10, prec="fp32", order="h_first", stream=None,
 
     p, n = V.shape
     r = W.shape[1]
-    cfg = make_config(p, n, r, eps, prec, order, split_k=split_k)
+    cfg = make_config(p, n, r, eps, prec, order, split_k=split_k, model=model)
     f = ctypes.c_double()
     st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else ctypes.c_void_p()
     _check(lib.nmf_solve(ctypes.byref(cfg), ptr(V), ptr(W), ptr(H), int(iters),

@@ -54,6 +54,7 @@ STREAM_WSTAR = 3
 STREAM_HSTAR = 4
 STREAM_NOISE = 5
 STREAM_SHAPES = 6
+STREAM_COUNTS = 7
 
 BASE_SEED = 20100316
 
@@ -219,6 +220,28 @@ def planted_problem(p: int, n: int, r: int, seed: int, sigma: float = 0.01,
     return Problem(name, V, W0, H0, r, iters, eps, seed)
 
 
+def poisson_counts(seed: int, stream: int, lam: np.ndarray) -> np.ndarray:
+    """Counts v_ij ~ Poisson(lam_ij), float32.  Drawn with numpy's Generator
+    seeded by (seed, stream): reproducible within one numpy version (the
+    tests draw the inputs once per process for both sides)."""
+    rng = np.random.default_rng([int(seed), int(stream)])
+    return rng.poisson(lam).astype(np.float32)
+
+
+def counts_problem(p: int, n: int, r: int, seed: int, mean: float = 5.0,
+                   iters: int = 20, name: str = "counts",
+                   eps: float = 1e-10) -> Problem:
+    """The Poisson model's workload: counts v_ij ~ Poisson(lam_ij) with
+    lam = W* H* scaled to mean ``mean`` (W*, H* iid Gamma(1,1)); Algorithm 1's
+    uniform(0,1) start."""
+    Ws = exponential(seed, STREAM_WSTAR, (p, r)).astype(np.float64)
+    Hs = exponential(seed, STREAM_HSTAR, (r, n)).astype(np.float64)
+    lam = (Ws @ Hs) * (mean / r)
+    V = poisson_counts(seed, STREAM_COUNTS, lam)
+    W0, H0 = starting_factors(seed, p, n, r)
+    return Problem(name, V, W0, H0, r, iters, eps, seed)
+
+
 def exact_planted(p: int, n: int, r: int, seed: int) -> Problem:
     """V = W0 H0 exactly representable: W0 and H0 hold small integers on a
     power-of-two grid so that every product and partial sum is exact in
@@ -240,6 +263,7 @@ TALL = dict(name="tall_65536x4096", p=65536, n=4096, iters=20)
 LARGE = dict(name="large_131072x16384_r64", p=131072, n=16384, r=64, iters=20)
 BATCH = dict(name="batched_512", count=512, pmin=64, pmax=2048, rmin=4, rmax=32,
              iters=100)
+COUNTS = dict(name="counts_8192x8192_r50", p=8192, n=8192, r=50, iters=20)
 
 
 def tall(r: int, seed: int = BASE_SEED + 2, iters: int = 20) -> Problem:
@@ -282,3 +306,8 @@ def batch(count: int = 512, seed: int = BASE_SEED + 3, iters: int = 100,
         probs.append(uniform_problem(p, n, r, seed * 1000 + b, iters,
                                      f"batch{b}_{p}x{n}_r{r}"))
     return probs
+
+
+def counts(seed: int = BASE_SEED + 5, iters: int = 20) -> Problem:
+    c = COUNTS
+    return counts_problem(c["p"], c["n"], c["r"], seed, 5.0, iters, c["name"])
