@@ -66,7 +66,7 @@ def step(V, W, H, eps=1e-10):
     Returns (W', H') in float64."""
     V, W, H = _f64(V), _f64(W), _f64(H)
     B = W @ H
-    Q = V / (B + eps)                     # v_ij / b_ij
+    Q = np.divide(V, B + eps, out=np.zeros_like(V), where=V > 0)   # v_ij / b_ij, 0 if v_ij = 0
     num_w = Q @ H.T                       # sum_j v_ij h_kj / b_ij   (p x r)
     num_h = W.T @ Q                       # sum_i v_ij w_ik / b_ij   (r x n)
     den_w = H.sum(axis=1)                 # sum_j h_kj               (r)

@@ -32,24 +32,11 @@ namespace {
 constexpr int kPT = 64;          // tile edge (rows and columns of V)
 constexpr int kPThreads = 256;   // 16 x 16 threads, a 4 x 4 sub-tile each
 constexpr int kPMaxRank = 64;
+constexpr int kLW = kPT + 4;     // row stride of Wt and Qs (16-byte rows)
 
-struct PoisShape {
-  int r, r4;                     // rank, rank rounded up to 4
-  int lgop;                      // row stride of the GEMM2 operand tile
-  __device__ __host__ int wt() const { return 0; }                     // [r][64]
-  __device__ __host__ int hs() const { return r * kPT; }               // [r][64]
-  __device__ __host__ int gop() const { return 2 * r * kPT; }          // [64][lgop]
-  __device__ __host__ int qs() const { return 2 * r * kPT + kPT * lgop; }  // [64][68]
-  __device__ __host__ int floats() const { return qs() + kPT * (kPT + 4); }
-};
-
-__host__ __device__ inline PoisShape pois_shape(int r) {
-  PoisShape s;
-  s.r = r;
-  s.r4 = (r + 3) & ~3;
-  s.lgop = s.r4 + 4;
-  return s;
-}
+// Shared memory of a pass block: Wt[r][kLW] (W_I transposed), Hs[r][64]
+// (H_J), Qs[64][kLW] (q of the tile, row-major).
+__host__ __device__ inline int pois_floats(int r) { return r * kLW + r * kPT + kPT * kLW; }
 
 // Row sums of H (which = 0: den of the W update) or column sums of W
 // (which = 1: den of the H update) for rank k = blockIdx.x / 2 ... in float64.
@@ -92,34 +79,23 @@ __device__ __forceinline__ void load_v(const float* __restrict__ V, int64_t ldv,
   }
 }
 
-// Stages W rows [i0, i0 + 64) as Wt[k][i] (GEMM1) and, when gop != nullptr,
-// as gop[i][k] (GEMM2); H columns [j0, j0 + 64) as Hs[k][j] and gop[j][k].
-// Zero outside the factors and for ranks r .. r4-1 of gop.  Each layout has
-// its own loop, with consecutive threads on consecutive shared-memory words
-// (the transposing reads hit the L1 copy of the same small block).
-__device__ __forceinline__ void stage_w(const float* __restrict__ W, int64_t p, int r, int r4,
-                                        int lgop, int64_t i0, float* Wt, float* gop) {
-  for (int idx = threadIdx.x; idx < r * kPT; idx += kPThreads) {
-    const int k = idx / kPT, i = idx - k * kPT;
-    Wt[idx] = i0 + i < p ? W[(i0 + i) * r + k] : 0.f;
+// Stages W rows [i0, i0 + 64) as Wt[k][i] (reads along the rows of W, so
+// the writes go down the columns of Wt: a stride of kLW words, four-way
+// bank conflicts) and H columns [j0, j0 + 64) as Hs[k][j] (both along
+// rows).  Zero outside the factors.
+__device__ __forceinline__ void stage_w(const float* __restrict__ W, int64_t p, int r,
+                                        int64_t i0, float* Wt) {
+  for (int idx = threadIdx.x; idx < kPT * r; idx += kPThreads) {
+    const int i = idx / r, k = idx - i * r;
+    Wt[k * kLW + i] = i0 + i < p ? W[(i0 + i) * r + k] : 0.f;
   }
-  if (gop)
-    for (int idx = threadIdx.x; idx < kPT * r4; idx += kPThreads) {
-      const int i = idx / r4, k = idx - i * r4;
-      gop[i * lgop + k] = (k < r && i0 + i < p) ? W[(i0 + i) * r + k] : 0.f;
-    }
 }
-__device__ __forceinline__ void stage_h(const float* __restrict__ H, int64_t n, int r, int r4,
-                                        int lgop, int64_t j0, float* Hs, float* gop) {
+__device__ __forceinline__ void stage_h(const float* __restrict__ H, int64_t n, int r,
+                                        int64_t j0, float* Hs) {
   for (int idx = threadIdx.x; idx < r * kPT; idx += kPThreads) {
     const int k = idx / kPT, j = idx - k * kPT;
     Hs[idx] = j0 + j < n ? H[(int64_t)k * n + j0 + j] : 0.f;
   }
-  if (gop)
-    for (int idx = threadIdx.x; idx < kPT * r4; idx += kPThreads) {
-      const int j = idx / r4, k = idx - j * r4;
-      gop[j * lgop + k] = (k < r && j0 + j < n) ? H[(int64_t)k * n + j0 + j] : 0.f;
-    }
 }
 
 // Knuth's two-sum: s + e = a + b exactly (round to nearest).
@@ -133,18 +109,23 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // MODE 1: block = (column panel J, segment of row tiles); numerator of H.
 // part: MODE 0 [seg][p][r], MODE 1 [seg][n][r] (float64).  Ranks above 64
 // are not served (pois_supported).
+//
+// Per tile: GEMM1 b = W_I H_J (thread: rows 4 ty .. 4 ty + 3, columns
+// 4 tx .. 4 tx + 3, K = r), q into Qs, then GEMM2 over the tile's 64 entries
+// of K, four at a time so that every operand load is 16 bytes:
+//   MODE 0: acc[x][y] += sum_u q[g + 16 x][j + u] h[4 c + y][j + u]
+//           (rows g + 16 x: consecutive lanes on consecutive rows of Qs)
+//   MODE 1: acc[x][y] += sum_u q[i + u][4 g + x] w[i + u][4 c + y]
+// with g = tid % 16 and c = tid / 16 (ranks 4 c .. 4 c + 3 < r4).
 template <int MODE>
 __global__ void __launch_bounds__(kPThreads)
 k_pois_pass(const float* __restrict__ V, int64_t ldv, const float* __restrict__ W,
             const float* __restrict__ H, int64_t p, int64_t n, int r, float eps, int segs,
             double* __restrict__ part) {
   extern __shared__ float sm[];
-  const PoisShape sh = pois_shape(r);
-  float* Wt = sm + sh.wt();
-  float* Hs = sm + sh.hs();
-  float* Gop = sm + sh.gop();
-  float* Qs = sm + sh.qs();
-  constexpr int LQ = kPT + 4;
+  float* Wt = sm;
+  float* Hs = sm + r * kLW;
+  float* Qs = Hs + r * kPT;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const int panel = blockIdx.x / segs, seg = blockIdx.x - panel * segs;
   const int64_t panel0 = (int64_t)panel * kPT;
@@ -153,14 +134,18 @@ k_pois_pass(const float* __restrict__ V, int64_t ldv, const float* __restrict__ 
   const int t0 = (int)((int64_t)seg * ntiles / segs);
   const int t1 = (int)((int64_t)(seg + 1) * ntiles / segs);
   const bool vec = (ldv % 4 == 0) && (reinterpret_cast<uintptr_t>(V) % 16 == 0);
-  // GEMM2 item of this thread: rows (MODE 0) or columns (MODE 1) 4 g .. 4 g + 3
-  // of the panel, ranks 4 c .. 4 c + 3
+  const int r4 = (r + 3) & ~3;
   const int g = tid & 15, c = tid >> 4;
-  const bool item = 4 * c < sh.r4;
+  const bool item = 4 * c < r4;
+  // ranks of this thread's GEMM2 item, clamped into the staged rows (the
+  // products of ranks r .. r4-1 are formed and discarded)
+  int ky[4];
+#pragma unroll
+  for (int y = 0; y < 4; ++y) ky[y] = min(4 * c + y, r - 1);
 
   // the panel's resident factor block
-  if (MODE == 0) stage_w(W, p, r, sh.r4, sh.lgop, panel0, Wt, nullptr);
-  else stage_h(H, n, r, sh.r4, sh.lgop, panel0, Hs, nullptr);
+  if (MODE == 0) stage_w(W, p, r, panel0, Wt);
+  else stage_h(H, n, r, panel0, Hs);
 
   // the segment's running sums, compensated across tiles: hi + lo
   float tot[4][4], err[4][4];
@@ -176,8 +161,8 @@ k_pois_pass(const float* __restrict__ V, int64_t ldv, const float* __restrict__ 
     float v[4][4];
     load_v(V, ldv, p, n, i0, j0, ty, tx, vec, v);
     __syncthreads();   // the previous tile's operands are consumed
-    if (MODE == 0) stage_h(H, n, r, sh.r4, sh.lgop, j0, Hs, Gop);
-    else stage_w(W, p, r, sh.r4, sh.lgop, i0, Wt, Gop);
+    if (MODE == 0) stage_h(H, n, r, j0, Hs);
+    else stage_w(W, p, r, i0, Wt);
     __syncthreads();
 
     // GEMM1: b = W_I H_J for rows 4 ty.., columns 4 tx..
@@ -188,7 +173,7 @@ k_pois_pass(const float* __restrict__ V, int64_t ldv, const float* __restrict__ 
       for (int e = 0; e < 4; ++e) b[a][e] = 0.f;
 #pragma unroll 4
     for (int k = 0; k < r; ++k) {
-      const float4 w4 = *reinterpret_cast<const float4*>(&Wt[k * kPT + 4 * ty]);
+      const float4 w4 = *reinterpret_cast<const float4*>(&Wt[k * kLW + 4 * ty]);
       const float4 h4 = *reinterpret_cast<const float4*>(&Hs[k * kPT + 4 * tx]);
       const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
       const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
@@ -197,36 +182,59 @@ k_pois_pass(const float* __restrict__ V, int64_t ldv, const float* __restrict__ 
 #pragma unroll
         for (int e = 0; e < 4; ++e) b[a][e] = fmaf(wv[a], hv[e], b[a][e]);
     }
-    // q = v / (b + eps); zero where v is zero.  MODE 0 stores Q^T [j][i],
-    // MODE 1 stores Q [i][j].
+    // q = v / (b + eps), zero where v is zero; row-major into Qs.  q only
+    // weights the sums of the numerators, so the fast division serves: within
+    // two ulps for divisors in [2^-126, 2^126] (the default eps = 1e-10 keeps
+    // b + eps above the lower end).
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a) {
+      float q[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float q = v[a][e] == 0.f ? 0.f : div_rn(v[a][e], __fadd_rn(b[a][e], eps));
-        if (MODE == 0) Qs[(4 * tx + e) * LQ + 4 * ty + a] = q;
-        else Qs[(4 * ty + a) * LQ + 4 * tx + e] = q;
-      }
+      for (int e = 0; e < 4; ++e)
+        q[e] = v[a][e] == 0.f ? 0.f : __fdividef(v[a][e], __fadd_rn(b[a][e], eps));
+      *reinterpret_cast<float4*>(&Qs[(4 * ty + a) * kLW + 4 * tx]) =
+          make_float4(q[0], q[1], q[2], q[3]);
+    }
     __syncthreads();
 
-    // GEMM2 over the tile's 64 entries of K (columns for MODE 0, rows for
-    // MODE 1): acc[x][y] for rows/columns 4 g + x and ranks 4 c + y.
     if (item) {
       float acc[4][4];
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
         for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
-#pragma unroll 4
-      for (int kk = 0; kk < kPT; ++kk) {
-        const float4 q4 = *reinterpret_cast<const float4*>(&Qs[kk * LQ + 4 * g]);
-        const float4 f4 = *reinterpret_cast<const float4*>(&Gop[kk * sh.lgop + 4 * c]);
-        const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
-        const float fv[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll 2
+      for (int kk = 0; kk < kPT; kk += 4) {
+        float qa[4][4], fa[4][4];
+        if (MODE == 0) {
 #pragma unroll
-        for (int x = 0; x < 4; ++x)
+          for (int x = 0; x < 4; ++x) {
+            const float4 q4 = *reinterpret_cast<const float4*>(&Qs[(g + 16 * x) * kLW + kk]);
+            qa[x][0] = q4.x; qa[x][1] = q4.y; qa[x][2] = q4.z; qa[x][3] = q4.w;
+          }
 #pragma unroll
-          for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(qv[x], fv[y], acc[x][y]);
+          for (int y = 0; y < 4; ++y) {
+            const float4 f4 = *reinterpret_cast<const float4*>(&Hs[ky[y] * kPT + kk]);
+            fa[y][0] = f4.x; fa[y][1] = f4.y; fa[y][2] = f4.z; fa[y][3] = f4.w;
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 q4 = *reinterpret_cast<const float4*>(&Qs[(kk + u) * kLW + 4 * g]);
+            qa[0][u] = q4.x; qa[1][u] = q4.y; qa[2][u] = q4.z; qa[3][u] = q4.w;
+          }
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            const float4 f4 = *reinterpret_cast<const float4*>(&Wt[ky[y] * kLW + kk]);
+            fa[y][0] = f4.x; fa[y][1] = f4.y; fa[y][2] = f4.z; fa[y][3] = f4.w;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(qa[x][u], fa[y][u], acc[x][y]);
       }
 #pragma unroll
       for (int x = 0; x < 4; ++x)
@@ -244,7 +252,7 @@ k_pois_pass(const float* __restrict__ V, int64_t ldv, const float* __restrict__ 
     double* dst = part + (int64_t)seg * extent * r;
 #pragma unroll
     for (int x = 0; x < 4; ++x) {
-      const int64_t m = panel0 + 4 * g + x;
+      const int64_t m = panel0 + (MODE == 0 ? g + 16 * x : 4 * g + x);
       if (m >= extent) continue;
 #pragma unroll
       for (int y = 0; y < 4; ++y) {
@@ -327,7 +335,7 @@ __global__ void k_pois_sum(const double* __restrict__ partials, int nparts,
 
 bool pois_supported(int r) { return r >= 1 && r <= kPMaxRank; }
 
-static size_t pois_smem_bytes(int r) { return (size_t)pois_shape(r).floats() * sizeof(float); }
+static size_t pois_smem_bytes(int r) { return (size_t)pois_floats(r) * sizeof(float); }
 
 PoisPlan pois_plan(int64_t p, int64_t n, int r, int sms) {
   PoisPlan pl;
