@@ -23,6 +23,7 @@
 // b is formed twice (once per pass), so an iteration is 8pnr flops.  Every
 // sum runs in a fixed order: the result is deterministic.
 #include <cstdint>
+#include <climits>
 
 #include "nmf_internal.cuh"
 
@@ -32,6 +33,7 @@ namespace {
 constexpr int kPT = 64;          // tile edge (rows and columns of V)
 constexpr int kPThreads = 256;   // 16 x 16 threads, a 4 x 4 sub-tile each
 constexpr int kPMaxRank = 64;
+static_assert(kPMaxRank <= 64, "stage_w gives each rank one of 64 lanes");
 constexpr int kLW = kPT + 4;     // row stride of Wt and Qs (16-byte rows)
 
 // Shared memory of a pass block: Wt[r][kLW] (W_I transposed), Hs[r][64]
@@ -79,16 +81,17 @@ __device__ __forceinline__ void load_v(const float* __restrict__ V, int64_t ldv,
   }
 }
 
-// Stages W rows [i0, i0 + 64) as Wt[k][i] (reads along the rows of W, so
-// the writes go down the columns of Wt: a stride of kLW words, four-way
-// bank conflicts) and H columns [j0, j0 + 64) as Hs[k][j] (both along
-// rows).  Zero outside the factors.
+// Stages W rows [i0, i0 + 64) as Wt[k][i] and H columns [j0, j0 + 64) as
+// Hs[k][j], zero outside the factors.  W: thread t reads rank t % 64 of row
+// t / 64 (+4 per pass), so a warp reads along a row of W and writes down a
+// column of Wt (stride kLW words: four-way bank conflicts); no division by
+// the runtime rank.  H: along rows on both sides.
 __device__ __forceinline__ void stage_w(const float* __restrict__ W, int64_t p, int r,
                                         int64_t i0, float* Wt) {
-  for (int idx = threadIdx.x; idx < kPT * r; idx += kPThreads) {
-    const int i = idx / r, k = idx - i * r;
+  const int k = threadIdx.x & 63;
+  if (k >= r) return;
+  for (int i = threadIdx.x >> 6; i < kPT; i += kPThreads / 64)
     Wt[k * kLW + i] = i0 + i < p ? W[(i0 + i) * r + k] : 0.f;
-  }
 }
 __device__ __forceinline__ void stage_h(const float* __restrict__ H, int64_t n, int r,
                                         int64_t j0, float* Hs) {
@@ -339,20 +342,34 @@ static size_t pois_smem_bytes(int r) { return (size_t)pois_floats(r) * sizeof(fl
 
 PoisPlan pois_plan(int64_t p, int64_t n, int r, int sms) {
   PoisPlan pl;
+  pl.smem = (int)pois_smem_bytes(r);
   const int64_t tp = (p + kPT - 1) / kPT, tn = (n + kPT - 1) / kPT;
-  // about four resident blocks per SM in each pass
-  const int64_t target = 4 * (int64_t)sms;
+  // Resident blocks of a pass (both instances have the same footprint).
+  int per_sm = 0;
+  if (cudaFuncSetAttribute(k_pois_pass<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           pl.smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pois_pass<0>, kPThreads,
+                                                    (size_t)pl.smem) != cudaSuccess)
+    per_sm = 1;
+  (void)cudaGetLastError();
+  const int64_t slots = (int64_t)sms * (per_sm < 1 ? 1 : per_sm);
+  // Segments per panel: the block count comes in waves of `slots`, and a
+  // block's time is its tiles plus about one tile of staging and partial
+  // writing; take the split with the least waves x (tiles + 1), at most 64.
   auto segs = [&](int64_t panels, int64_t tiles) {
-    int64_t s = (target + panels - 1) / panels;
-    if (s > tiles) s = tiles;
-    if (s < 1) s = 1;
-    return (int)s;
+    int64_t best = 1, best_cost = INT64_MAX;
+    const int64_t smax = tiles < 64 ? tiles : 64;
+    for (int64_t s = 1; s <= smax; ++s) {
+      const int64_t waves = (panels * s + slots - 1) / slots;
+      const int64_t cost = waves * ((tiles + s - 1) / s + 1);
+      if (cost < best_cost) { best_cost = cost; best = s; }
+    }
+    return (int)best;
   };
   pl.segW = segs(tp, tn);
   pl.segH = segs(tn, tp);
   pl.gridW = (int)(tp * pl.segW);
   pl.gridH = (int)(tn * pl.segH);
-  pl.smem = (int)pois_smem_bytes(r);
   return pl;
 }
 
