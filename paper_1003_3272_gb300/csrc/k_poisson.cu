@@ -293,31 +293,73 @@ __global__ void k_pois_update(float* __restrict__ W, float* __restrict__ H, int6
   }
 }
 
-// L = sum_ij [v_ij ln b_ij - b_ij] in float64 (b formed in float64), per
-// block partials in a fixed order; 0 ln 0 = 0.
-constexpr int kLBlocks = 1216;
+// L = sum_ij [v_ij ln b_ij - b_ij], 0 ln 0 = 0, over 64 x 64 tiles (block b
+// takes tiles b, b + grid, ...; the grid is fixed, so the order is too).
+// b_ij = sum_k w_ik h_kj as an unevaluated float32 pair hi + lo by the
+// compensated dot product of Ogita, Rump and Oishi (2005, "Dot2": exact
+// products by FMA, Knuth's two-sum on the running sum), within a few units
+// of 2^-48 relative of the exact sum; then hi + lo in float64, its float64
+// logarithm and the float64 sum.
+constexpr int kLBlocks = 2 * 152;
 __global__ void __launch_bounds__(kPThreads)
 k_pois_loglik(const float* __restrict__ V, int64_t ldv, const float* __restrict__ W,
               const float* __restrict__ H, int64_t p, int64_t n, int r,
               double* __restrict__ partials) {
+  extern __shared__ float sm[];
+  float* Wt = sm;
+  float* Hs = sm + r * kLW;
   __shared__ double red[kPThreads];
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int64_t tp = (p + kPT - 1) / kPT, tn = (n + kPT - 1) / kPT;
+  const bool vec = (ldv % 4 == 0) && (reinterpret_cast<uintptr_t>(V) % 16 == 0);
   double s = 0.0;
-  const int64_t total = p * n;
-  for (int64_t idx = (int64_t)blockIdx.x * kPThreads + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * kPThreads) {
-    const int64_t i = idx / n, j = idx - i * n;
-    double b = 0.0;
-    for (int k = 0; k < r; ++k) b = fma((double)W[i * r + k], (double)H[(int64_t)k * n + j], b);
-    const double v = (double)V[i * ldv + j];
-    s += (v != 0.0 ? v * log(b) : 0.0) - b;
+  for (int64_t t = blockIdx.x; t < tp * tn; t += gridDim.x) {
+    const int64_t i0 = (t / tn) * kPT, j0 = (t % tn) * kPT;
+    float v[4][4];
+    load_v(V, ldv, p, n, i0, j0, ty, tx, vec, v);
+    __syncthreads();
+    stage_w(W, p, r, i0, Wt);
+    stage_h(H, n, r, j0, Hs);
+    __syncthreads();
+    float hi[4][4], lo[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) hi[a][e] = lo[a][e] = 0.f;
+    for (int k = 0; k < r; ++k) {
+      const float4 w4 = *reinterpret_cast<const float4*>(&Wt[k * kLW + 4 * ty]);
+      const float4 h4 = *reinterpret_cast<const float4*>(&Hs[k * kPT + 4 * tx]);
+      const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+      const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float pr = __fmul_rn(wv[a], hv[e]);
+          const float pe = fmaf(wv[a], hv[e], -pr);          // exact product error
+          float sum, se;
+          two_sum(hi[a][e], pr, sum, se);
+          hi[a][e] = sum;
+          lo[a][e] = __fadd_rn(lo[a][e], __fadd_rn(pe, se));
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (i0 + 4 * ty + a >= p || j0 + 4 * tx + e >= n) continue;
+        const double b = (double)hi[a][e] + (double)lo[a][e];
+        const double x = (double)v[a][e];
+        s += (x != 0.0 ? x * log(b) : 0.0) - b;
+      }
   }
-  red[threadIdx.x] = s;
+  red[tid] = s;
   __syncthreads();
   for (int w = kPThreads / 2; w >= 1; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    if (tid < w) red[tid] += red[tid + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+  if (tid == 0) partials[blockIdx.x] = red[0];
 }
 
 __global__ void k_pois_sum(const double* __restrict__ partials, int nparts,
@@ -398,7 +440,11 @@ cudaError_t pois_iteration(const PoisPlan& pl, const float* V, int64_t ldv, floa
 
 cudaError_t pois_loglik(const float* V, int64_t ldv, const float* W, const float* H, int64_t p,
                         int64_t n, int r, double* partials, double* out, cudaStream_t st) {
-  k_pois_loglik<<<kLBlocks, kPThreads, 0, st>>>(V, ldv, W, H, p, n, r, partials);
+  const int smem = (r * kLW + r * kPT) * (int)sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_pois_loglik, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem);
+  if (e != cudaSuccess) return e;
+  k_pois_loglik<<<kLBlocks, kPThreads, smem, st>>>(V, ldv, W, H, p, n, r, partials);
   k_pois_sum<<<1, kPThreads, 0, st>>>(partials, kLBlocks, out);
   return cudaGetLastError();
 }
