@@ -127,21 +127,26 @@ nmf_status nmf_config_default(nmf_config* cfg, int64_t p, int64_t n, int32_t r);
 nmf_status nmf_init(const nmf_config* cfg, const float* V, float* W, float* H,
                     void* stream, nmf_ctx** out);
 
-/* Run `iters` >= 0 MM iterations (Algorithm 1's loop body, in cfg.order),
- * updating W and H in place.  Asynchronous on the context's stream.       */
+/* Run `iters` >= 0 MM iterations (Algorithm 1's loop body, in cfg.order;
+ * for NMF_MODEL_POISSON the simultaneous square-root update), updating W
+ * and H in place.  Asynchronous on the context's stream.                   */
 nmf_status nmf_step(nmf_ctx* ctx, int iters);
 
 /* One block update only: which = 0 updates H (Eq. (3.4) in the paper's
  * letters), which = 1 updates W (Eq. (3.3)).  nmf_step(ctx, 1) equals the
- * two half steps in cfg.order.  Asynchronous.                               */
+ * two half steps in cfg.order.  Asynchronous.  NMF_EUNSUPPORTED for the
+ * Poisson model (its update has no half steps).                            */
 nmf_status nmf_half_step(nmf_ctx* ctx, int which);
 
 /* f = ||V - W H||_F^2 (Eq. (3.1)) at the current W, H, as a direct residual
- * summed in float64 in a fixed order; *f_out is host memory.  Synchronises
- * the stream.                                                               */
+ * summed in float64 in a fixed order; for NMF_MODEL_POISSON the
+ * loglikelihood L = sum_ij [v_ij ln (WH)_ij - (WH)_ij] (0 ln 0 = 0) instead,
+ * (WH)_ij by a compensated float32 dot product, the rest in float64.
+ * *f_out is host memory.  Synchronises the stream.                          */
 nmf_status nmf_objective(nmf_ctx* ctx, double* f_out);
 
-/* Algorithm 1 with Section 3's stopping rule: iterate until
+/* Algorithm 1 with Section 3's stopping rule (f is the model's objective:
+ * the Frobenius residual, or L for the Poisson model): iterate until
  * |f_k - f_{k-1}| / (|f_{k-1}| + 1) < tol or max_iters iterations, testing
  * the objective every `check_every` >= 1 iterations.  *iters_done and *f_out
  * (host) receive the count and the last objective.  Synchronises.          */
@@ -167,7 +172,8 @@ nmf_status nmf_converge(nmf_ctx* ctx, int max_iters, double tol, int check_every
 nmf_status nmf_restart(nmf_ctx* ctx, uint64_t seed);
 
 /* Copy the current Gram matrix (which = 0: W^T W, which = 1: H H^T) into
- * host memory `out` (r*r doubles, row-major).  Synchronises.              */
+ * host memory `out` (r*r doubles, row-major).  Synchronises.
+ * NMF_EUNSUPPORTED for the Poisson model (it forms no Gram matrices).     */
 nmf_status nmf_read_gram(nmf_ctx* ctx, int which, double* out);
 
 /* One-call solve: V, W, H may each be host or device pointers (detected per
@@ -222,7 +228,9 @@ nmf_status nmf_gram_noalloc(const float* F, int32_t layout, int64_t M, int64_t l
  * This hook makes that happen on purpose for the next half step: it gives
  * the launch's grid-wide publication waits a target the device counter
  * never reaches, so that every block's wait runs out (about 3 s in all).
- * The context stays usable afterwards.  NMF_EINVAL for ctx == NULL.        */
+ * The context stays usable afterwards.  NMF_EINVAL for ctx == NULL;
+ * NMF_EUNSUPPORTED for the Poisson model (its kernels have no grid-wide
+ * waits).                                                                  */
 nmf_status nmf_test_expire_next_wait(nmf_ctx* ctx);
 
 /* ---- Self-check of the update's division ----------------------------------
