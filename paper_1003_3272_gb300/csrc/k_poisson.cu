@@ -13,8 +13,7 @@
 //   k_pois_pass<0> per 64-row panel of V and a segment of its 64-column
 //                  tiles: b = W_I H_J (K = r), q = v / (b + eps), and the
 //                  numerator of W, q H_J^T (K = 64), summed over the
-//                  segment's tiles (float32 within a tile, compensated
-//                  two-sum across tiles, written out in float64);
+//                  segment's tiles in float32 and written out in float64;
 //   k_pois_pass<1> the same per 64-column panel and a segment of its row
 //                  tiles, with the numerator of H, W_I^T q;
 //   k_pois_update  both factors in place from the segment partials (summed
@@ -101,6 +100,48 @@ __device__ __forceinline__ void stage_h(const float* __restrict__ H, int64_t n, 
   }
 }
 
+// The next tile's streamed factor block, held in registers while the
+// current tile's GEMM2 runs (its loads then overlap the arithmetic):
+// MODE 0 H_J (r x 64; element tid + 256 m), MODE 1 W_I (64 x r; rank
+// tid % 64 of rows tid / 64 + 4 m, as stage_w).  Zero outside the factors.
+template <int MODE>
+struct NextBlock {
+  float x[16];
+  __device__ __forceinline__ void load(const float* __restrict__ W, const float* __restrict__ H,
+                                       int64_t p, int64_t n, int r, int64_t i0, int64_t j0) {
+    if (MODE == 0) {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int idx = threadIdx.x + kPThreads * m;
+        const int k = idx >> 6, j = idx & 63;
+        x[m] = (k < r && j0 + j < n) ? H[(int64_t)k * n + j0 + j] : 0.f;
+      }
+    } else {
+      const int k = threadIdx.x & 63;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int i = (threadIdx.x >> 6) + 4 * m;
+        x[m] = (k < r && i0 + i < p) ? W[(i0 + i) * r + k] : 0.f;
+      }
+    }
+  }
+  __device__ __forceinline__ void store(int r, float* Wt, float* Hs) const {
+    if (MODE == 0) {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int idx = threadIdx.x + kPThreads * m;
+        if (idx < r * kPT) Hs[idx] = x[m];
+      }
+    } else {
+      const int k = threadIdx.x & 63;
+      if (k < r) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) Wt[k * kLW + (threadIdx.x >> 6) + 4 * m] = x[m];
+      }
+    }
+  }
+};
+
 // Knuth's two-sum: s + e = a + b exactly (round to nearest).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
@@ -150,13 +191,17 @@ k_pois_pass(const float* __restrict__ V, int64_t ldv, const float* __restrict__ 
   if (MODE == 0) stage_w(W, p, r, panel0, Wt);
   else stage_h(H, n, r, panel0, Hs);
 
-  // the segment's running sums, compensated across tiles: hi + lo
-  float tot[4][4], err[4][4];
+  // the segment's running sums (float32 over its tiles)
+  float tot[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) tot[a][b] = err[a][b] = 0.f;
+    for (int b = 0; b < 4; ++b) tot[a][b] = 0.f;
 
+  NextBlock<MODE> nb;
+  if (t0 < t1)
+    nb.load(W, H, p, n, r, MODE == 0 ? panel0 : (int64_t)t0 * kPT,
+            MODE == 0 ? (int64_t)t0 * kPT : panel0);
   for (int t = t0; t < t1; ++t) {
     const int64_t o0 = (int64_t)t * kPT;
     const int64_t i0 = MODE == 0 ? panel0 : o0;
@@ -164,8 +209,7 @@ k_pois_pass(const float* __restrict__ V, int64_t ldv, const float* __restrict__ 
     float v[4][4];
     load_v(V, ldv, p, n, i0, j0, ty, tx, vec, v);
     __syncthreads();   // the previous tile's operands are consumed
-    if (MODE == 0) stage_h(H, n, r, j0, Hs);
-    else stage_w(W, p, r, i0, Wt);
+    nb.store(r, Wt, Hs);
     __syncthreads();
 
     // GEMM1: b = W_I H_J for rows 4 ty.., columns 4 tx..
@@ -199,6 +243,10 @@ k_pois_pass(const float* __restrict__ V, int64_t ldv, const float* __restrict__ 
           make_float4(q[0], q[1], q[2], q[3]);
     }
     __syncthreads();
+    if (t + 1 < t1) {
+      const int64_t o1 = o0 + kPT;
+      nb.load(W, H, p, n, r, MODE == 0 ? panel0 : o1, MODE == 0 ? o1 : panel0);
+    }
 
     if (item) {
       float acc[4][4];
@@ -242,11 +290,7 @@ k_pois_pass(const float* __restrict__ V, int64_t ldv, const float* __restrict__ 
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < 4; ++y) {
-          float e;
-          two_sum(tot[x][y], acc[x][y], tot[x][y], e);
-          err[x][y] = __fadd_rn(err[x][y], e);
-        }
+        for (int y = 0; y < 4; ++y) tot[x][y] = __fadd_rn(tot[x][y], acc[x][y]);
     }
   }
 
@@ -260,7 +304,7 @@ k_pois_pass(const float* __restrict__ V, int64_t ldv, const float* __restrict__ 
 #pragma unroll
       for (int y = 0; y < 4; ++y) {
         const int k = 4 * c + y;
-        if (k < r) dst[m * r + k] = (double)tot[x][y] + (double)err[x][y];
+        if (k < r) dst[m * r + k] = (double)tot[x][y];
       }
     }
   }
