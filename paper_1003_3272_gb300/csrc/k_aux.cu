@@ -235,10 +235,39 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) 
   err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// Sums block partials into *out once every block of the grid has written
+// its own: the block whose arrival on `done` is the last one adds them in
+// index order (a fixed order: deterministic) and re-arms the counter.
+__device__ __forceinline__ void last_block_sum(double part, double* __restrict__ partials,
+                                               unsigned int* done, double* __restrict__ out) {
+  __shared__ bool last;
+  __shared__ double red2[kObjThreads];
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = part;
+    __threadfence();
+    last = atomicAdd(done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+  for (unsigned i = threadIdx.x; i < gridDim.x; i += kObjThreads) s += __ldcg(&partials[i]);
+  red2[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kObjThreads / 2; w >= 1; w >>= 1) {
+    if ((int)threadIdx.x < w) red2[threadIdx.x] += red2[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *out = red2[0];
+    *done = 0u;
+  }
+}
+
 __global__ void __launch_bounds__(kObjThreads)
 k_objective(const float* __restrict__ V, int64_t ldv, const float* __restrict__ W,
             const float* __restrict__ H, int64_t p, int64_t n, int r,
-            double* __restrict__ partials) {
+            double* __restrict__ partials, unsigned int* done, double* __restrict__ out) {
   extern __shared__ float sm[];
   const int rp = (r + 1) & ~1;               // even
   const int LW = rp;                         // W row stride (even: 8-byte loads)
@@ -331,7 +360,8 @@ k_objective(const float* __restrict__ V, int64_t ldv, const float* __restrict__ 
     acc64 += (double)sq[0];
   }
 
-  // Block reduction in float64, fixed order.
+  // Block reduction in float64, fixed order; the grid's last block adds the
+  // partials.
   __shared__ double red[kObjThreads];
   red[tid] = acc64;
   __syncthreads();
@@ -339,21 +369,7 @@ k_objective(const float* __restrict__ V, int64_t ldv, const float* __restrict__ 
     if (tid < w) red[tid] += red[tid + w];
     __syncthreads();
   }
-  if (tid == 0) partials[blockIdx.x] = red[0];
-}
-
-__global__ void k_sum_partials(const double* __restrict__ partials, int nparts,
-                               double* __restrict__ out) {
-  __shared__ double red[256];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += 256) s += partials[i];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = 128; w >= 1; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = red[0];
+  last_block_sum(red[0], partials, done, out);
 }
 
 // Section 3's stopping rule, |f_k - f_{k-1}| / (|f_{k-1}| + 1) < tol, taken
@@ -458,7 +474,9 @@ cudaError_t launch_run_test(RunState* s, const double* f_dev, int iters,
   return cudaGetLastError();
 }
 
-int objective_parts() { return kObjBlocks; }
+// Partials plus the arrival counter of the last-block sum (zeroed at
+// allocation, re-armed by every launch).
+int objective_parts() { return kObjBlocks + 1; }
 
 cudaError_t launch_objective(const float* V, int64_t ldv, const float* W, const float* H,
                              int64_t p, int64_t n, int r, double* partials, int nparts,
@@ -468,8 +486,12 @@ cudaError_t launch_objective(const float* V, int64_t ldv, const float* W, const 
   cudaError_t e = cudaFuncSetAttribute(k_objective, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_objective<<<nparts, kObjThreads, smem, st>>>(V, ldv, W, H, p, n, r, partials);
-  k_sum_partials<<<1, 256, 0, st>>>(partials, nparts, f_dev);
+  // one block per tile up to kObjBlocks; the counter sits after the partials
+  const int64_t tiles = ceil_div(p, kObjBM) * ceil_div(n, kObjBN);
+  const int grid = (int)(tiles < kObjBlocks ? (tiles < 1 ? 1 : tiles) : kObjBlocks);
+  if (nparts < kObjBlocks + 1) return cudaErrorInvalidValue;
+  unsigned int* done = reinterpret_cast<unsigned int*>(partials + kObjBlocks);
+  k_objective<<<grid, kObjThreads, smem, st>>>(V, ldv, W, H, p, n, r, partials, done, f_dev);
   return cudaGetLastError();
 }
 

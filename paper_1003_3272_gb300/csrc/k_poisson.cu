@@ -348,7 +348,7 @@ constexpr int kLBlocks = 2 * 152;
 __global__ void __launch_bounds__(kPThreads)
 k_pois_loglik(const float* __restrict__ V, int64_t ldv, const float* __restrict__ W,
               const float* __restrict__ H, int64_t p, int64_t n, int r,
-              double* __restrict__ partials) {
+              double* __restrict__ partials, unsigned int* done, double* __restrict__ out) {
   extern __shared__ float sm[];
   float* Wt = sm;
   float* Hs = sm + r * kLW;
@@ -403,21 +403,30 @@ k_pois_loglik(const float* __restrict__ V, int64_t ldv, const float* __restrict_
     if (tid < w) red[tid] += red[tid + w];
     __syncthreads();
   }
-  if (tid == 0) partials[blockIdx.x] = red[0];
-}
-
-__global__ void k_pois_sum(const double* __restrict__ partials, int nparts,
-                           double* __restrict__ out) {
-  __shared__ double red[kPThreads];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += kPThreads) s += partials[i];
-  red[threadIdx.x] = s;
+  // the grid's last block adds the block partials in index order (fixed:
+  // deterministic) and re-arms the counter
+  __shared__ bool last;
+  if (tid == 0) {
+    partials[blockIdx.x] = red[0];
+    __threadfence();
+    last = atomicAdd(done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t = 0.0;
+  for (unsigned i = tid; i < gridDim.x; i += kPThreads) t += __ldcg(&partials[i]);
+  __syncthreads();
+  red[tid] = t;
   __syncthreads();
   for (int w = kPThreads / 2; w >= 1; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    if (tid < w) red[tid] += red[tid + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = red[0];
+  if (tid == 0) {
+    *out = red[0];
+    *done = 0u;
+  }
 }
 
 }  // namespace
@@ -459,7 +468,8 @@ PoisPlan pois_plan(int64_t p, int64_t n, int r, int sms) {
   return pl;
 }
 
-int pois_loglik_parts() { return kLBlocks; }
+// Block partials plus the arrival counter of the last-block sum.
+int pois_loglik_parts() { return kLBlocks + 1; }
 
 cudaError_t pois_iteration(const PoisPlan& pl, const float* V, int64_t ldv, float* W, float* H,
                            int64_t p, int64_t n, int r, float eps, double* sums, double* partW,
@@ -488,8 +498,8 @@ cudaError_t pois_loglik(const float* V, int64_t ldv, const float* W, const float
   cudaError_t e = cudaFuncSetAttribute(k_pois_loglik, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        smem);
   if (e != cudaSuccess) return e;
-  k_pois_loglik<<<kLBlocks, kPThreads, smem, st>>>(V, ldv, W, H, p, n, r, partials);
-  k_pois_sum<<<1, kPThreads, 0, st>>>(partials, kLBlocks, out);
+  unsigned int* done = reinterpret_cast<unsigned int*>(partials + kLBlocks);
+  k_pois_loglik<<<kLBlocks, kPThreads, smem, st>>>(V, ldv, W, H, p, n, r, partials, done, out);
   return cudaGetLastError();
 }
 

@@ -584,7 +584,7 @@ nmf_status nmf_objective(nmf_ctx* c, double* f_out) {
   {
     ProfScope ps(c, 2);
     CK(launch_model_objective(c), "objective");
-    launched(2);
+    launched(1);
   }
   CK(cudaMemcpyAsync(c->f_host, c->f_dev, 8, cudaMemcpyDeviceToHost, c->st), "memcpy f");
   nmf_status s = check_device_error(c);
@@ -688,7 +688,7 @@ nmf_status nmf_converge(nmf_ctx* c, int max_iters, double tol, int check_every,
   {
     ProfScope ps(c, 2);
     CK(launch_model_objective(c), "objective");
-    launched(2);
+    launched(1);
   }
   CK(launch_run_init(c->run_dev, c->f_dev, max_iters, tol, c->st), "run init");
   launched(1);
@@ -697,8 +697,8 @@ nmf_status nmf_converge(nmf_ctx* c, int max_iters, double tol, int check_every,
      "memcpy run state");
   if ((s = check_device_error(c)) != NMF_OK) return s;
   const RunState r = *c->run_host;
-  // kernels the graph ran: two (Poisson: four) per iteration, three per test
-  launched((c->pois ? 4 : 2) * r.done + 3 * r.checks);
+  // kernels the graph ran: two (Poisson: four) per iteration, two per test
+  launched((c->pois ? 4 : 2) * r.done + 2 * r.checks);
   int done = r.done;
   double f = r.f;
   if (!r.stop && done < max_iters) {

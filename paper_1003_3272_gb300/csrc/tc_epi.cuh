@@ -441,10 +441,11 @@ __device__ void gram_rows(float* Qs, const float* Q, int layout, int64_t ldq_g, 
 }
 
 // Float64 sum, in a fixed order, of the `nparts` partials of entries
-// [e0, e1): thread h takes entry e0 + h % ne and partials g, g + ng, ...
-// (g = h / ne, ng = 192 / ne groups); the group sums are then added in
-// group order.  Writes G64 (r x r) and the zero-padded float32 copy Gpad.
-// `scratch` holds 192 doubles (shared).
+// [e0, e1), nb entries at a time: the helpers form ng groups per entry (ng
+// the largest power of two <= min(NH / nb, nparts)); group g adds partials
+// g, g + ng, g + 2 ng, ... (16 loads in flight), and the ng group sums are
+// added pairwise in a fixed tree (log2 ng rounds).  Writes G64 (r x r) and
+// the zero-padded float32 copy Gpad.  `scratch` holds NH doubles (shared).
 template <int RPAD, int NH = kHelpers>
 __device__ void gram_reduce_slice(const double* gpart, int nparts, int r, int e0, int e1,
                                   double* G64, float* Gpad, double* scratch, int h) {
@@ -453,10 +454,12 @@ __device__ void gram_reduce_slice(const double* gpart, int nparts, int r, int e0
   if (ne <= 0) return;
   for (int eb = e0; eb < e1; eb += NH) {
     const int nb = min(NH, e1 - eb);
-    const int ng = NH / nb;
+    const int cap = min(NH / nb, nparts);
+    int ng = 1;
+    while (2 * ng <= cap) ng *= 2;
     const int g = h / nb, e = eb + h % nb;
-    double s = 0.0;
     if (g < ng) {
+      double s = 0.0;
       for (int t0 = g; t0 < nparts; t0 += 16 * ng) {
         double v[16];
 #pragma unroll
@@ -471,9 +474,12 @@ __device__ void gram_reduce_slice(const double* gpart, int nparts, int r, int e0
       scratch[g * nb + (h % nb)] = s;
     }
     helper_sync<NH>();
+    for (int w = ng / 2; w >= 1; w >>= 1) {
+      if (g < w) scratch[g * nb + (h % nb)] += scratch[(g + w) * nb + (h % nb)];
+      helper_sync<NH>();
+    }
     if (h < nb) {
-      double tot = 0.0;
-      for (int gg = 0; gg < ng; ++gg) tot += scratch[gg * nb + h];
+      const double tot = scratch[h];
       G64[eb + h] = tot;
       Gpad[((eb + h) / r) * RPAD + ((eb + h) % r)] = (float)tot;
     }
