@@ -54,7 +54,32 @@ def test_config_struct_layout(lib):
     assert (cfg.p, cfg.n, cfg.r) == (10, 20, 3)
     assert cfg.eps == pytest.approx(1e-10)
     assert cfg.prec == nmf.FP32 and cfg.order == nmf.H_FIRST
+    assert cfg.model == nmf.GAUSSIAN
     assert ctypes.sizeof(nmf.Config) == 56
+    assert nmf.Config.model.offset == 52   # the last int32 of the header's struct
+
+
+@pytest.mark.parametrize("model,prec,r,want", [
+    (5, "fp32", 10, "EINVAL"),             # no such model
+    ("poisson", "bf16x3", 10, "EUNSUPPORTED"),   # the Poisson kernels are float32
+    ("poisson", "tf32", 10, "EUNSUPPORTED"),
+    ("poisson", "fp32", 65, "EUNSUPPORTED"),     # ranks up to 64
+])
+def test_model_requests_checked_on_the_host(lib, model, prec, r, want):
+    from paper_1003_3272_gb300 import nmf
+    cfg = nmf.make_config(100, 120, r, prec=prec, model=model)
+    ctx = ctypes.c_void_p(123)
+    dummy = ctypes.c_void_p(16)
+    st = lib.nmf_init(ctypes.byref(cfg), dummy, dummy, dummy, None, ctypes.byref(ctx))
+    assert st == getattr(nmf, want)
+    assert ctx.value is None
+
+
+def test_device_loop_rejects_bad_arguments(lib):
+    from paper_1003_3272_gb300 import nmf
+    done, f = ctypes.c_int(), ctypes.c_double()
+    assert lib.nmf_converge(None, 10, 1e-9, 1, ctypes.byref(done), ctypes.byref(f)) == nmf.EINVAL
+    assert lib.nmf_run(None, 10, 1e-9, 1, ctypes.byref(done), ctypes.byref(f)) == nmf.EINVAL
 
 
 @pytest.mark.parametrize("bad", [
