@@ -245,11 +245,6 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
     const int G = gridDim.x;
     ptx::pdl_wait();   // the factors of the previous half step are final
     const unsigned long long base = h == 0 ? launch_base(a.ctr, a.unit) + a.skew : 0ull;
-    if (cid < a.tiles) {
-      const int64_t row0 = (int64_t)cid * kBM + (int64_t)q * R;
-      const int rows = (int)max((int64_t)0, min((int64_t)R, a.M - row0));
-      tcepi::load_old<RPAD>(Os, a.ep, R, row0, rows, h);
-    }
     const int64_t q0 = (int64_t)blockIdx.x * a.QM / G;
     const int64_t q1 = (int64_t)(blockIdx.x + 1) * a.QM / G;
     tcepi::gram_rows<RPAD>(Qs, a.Q, a.q_layout, a.ldq, q0, q1, a.r,
@@ -257,6 +252,12 @@ k_stream_tc(const __grid_constant__ CUtensorMap tx_hi, const __grid_constant__ C
     __threadfence();
     tcepi::helper_sync();
     if (h == 0) atomicAdd(a.ctr, phase_add(G, a.unit));
+    // the first tile's old rows, while the other blocks arrive
+    if (cid < a.tiles) {
+      const int64_t row0 = (int64_t)cid * kBM + (int64_t)q * R;
+      const int rows = (int)max((int64_t)0, min((int64_t)R, a.M - row0));
+      tcepi::load_old<RPAD>(Os, a.ep, R, row0, rows, h);
+    }
     if (h == 0 && !wait_counter(a.ctr, base + a.unit)) atomicExch(&s_abort, 1);
     tcepi::helper_sync();
     if (!*(volatile int*)&s_abort) {
