@@ -54,6 +54,7 @@ struct F32Params {
   unsigned long long* ctr;
   unsigned long long unit;   // every launch adds 2 * unit (see k_stream_tc.cu)
   unsigned long long skew;
+  int old_first;             // see k_stream_tc.cu
   int* err;
 };
 
@@ -158,6 +159,17 @@ k_stream_f32(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUt
     const int G = gridDim.x;
     ptx::pdl_wait();
     const unsigned long long base = h == 0 ? launch_base(a.ctr, a.unit) + a.skew : 0ull;
+    // The first tile's old rows: before the Gram when the launch streams
+    // long (they are then off the critical path), else while the other
+    // blocks arrive at the Gram's first grid-wide step.
+    auto first_old = [&]() {
+      if (cid < a.tiles) {
+        const int64_t row0 = (int64_t)cid * kBM + (int64_t)q * R;
+        const int rows = (int)max((int64_t)0, min((int64_t)R, a.M - row0));
+        tcepi::load_old<RPAD, kNH>(Os, a.ep, R, row0, rows, h);
+      }
+    };
+    if (a.old_first) first_old();
     const int64_t q0 = (int64_t)blockIdx.x * a.QM / G;
     const int64_t q1 = (int64_t)(blockIdx.x + 1) * a.QM / G;
     tcepi::gram_rows<RPAD, kNH>(Qs, a.Q, a.q_layout, a.ldq, q0, q1, a.r,
@@ -165,12 +177,7 @@ k_stream_f32(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUt
     __threadfence();
     tcepi::helper_sync<kNH>();
     if (h == 0) atomicAdd(a.ctr, phase_add(G, a.unit));
-    // the first tile's old rows, while the other blocks arrive
-    if (cid < a.tiles) {
-      const int64_t row0 = (int64_t)cid * kBM + (int64_t)q * R;
-      const int rows = (int)max((int64_t)0, min((int64_t)R, a.M - row0));
-      tcepi::load_old<RPAD, kNH>(Os, a.ep, R, row0, rows, h);
-    }
+    if (!a.old_first) first_old();   // while the other blocks arrive
     if (h == 0 && !wait_counter(a.ctr, base + a.unit)) atomicExch(&s_abort, 1);
     tcepi::helper_sync<kNH>();
     if (!*(volatile int*)&s_abort) {
@@ -383,6 +390,7 @@ cudaError_t f32_launch(const TcPlan& pl, const EpiArgs& ep, const TcGram& gr, in
   prm.Q = gr.Q; prm.q_layout = gr.q_layout; prm.ldq = gr.ldq; prm.QM = gr.QM;
   prm.gpart = gr.gpart; prm.Gpad = gr.Gpad; prm.G64 = gr.G64;
   prm.ctr = gr.ctr; prm.unit = gr.unit; prm.skew = gr.skew;
+  prm.old_first = gr.old_first;
   prm.err = err;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)pl.grid, 1, 1);

@@ -473,6 +473,9 @@ nmf_status run_half(nmf_ctx* c, int which) {
     g.G64 = other == 0 ? c->GW64 : c->GH64;
     g.ctr = c->gctr;
     g.unit = c->gunit;
+    // long streams (V of 2^24 entries and more) hide the old rows' loads
+    // behind the Gram; short launches overlap them with its first grid step
+    g.old_first = c->p * c->n >= (int64_t)1 << 24 ? 1 : 0;
     g.skew = 0;
     if (!c->capturing) {   // skew: only from nmf_test_expire_next_wait
       g.skew = c->gctr_skew;

@@ -45,6 +45,8 @@ struct TcGram {
   unsigned long long unit;       // every launch adds 2 x unit; unit >= grid of every
                                  // launch on this counter (fixed for its lifetime)
   unsigned long long skew;       // added to the wait targets: 0 (test hook)
+  int old_first;                 // 1: load the first tile's old rows before the Gram
+                                 // (long launches), 0: during its first grid-wide step
 };
 
 nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, const void* Y_hi,
