@@ -157,3 +157,41 @@ def test_requests_the_model_does_not_serve():
         with pytest.raises(nmf.NMFError) as ei:
             m.gram(0)
         assert ei.value.status == nmf.EUNSUPPORTED
+
+
+def test_solve_with_host_buffers_and_restart():
+    """The one-call solve (host V, W, H copied in and out) and a seeded
+    restart serve the Poisson model: both equal the context's own steps."""
+    import torch
+    from paper_1003_3272_gb300 import nmf
+    pr = synth.counts_problem(150, 170, 6, seed=13)
+    Wh, Hh = pr.W0.copy(), pr.H0.copy()
+    L = nmf.solve(pr.V, Wh, Hh, 4, eps=pr.eps, model="poisson")
+    m, W, H = _ctx(pr)
+    with m:
+        m.step(4)
+        assert L == m.objective()
+        assert np.array_equal(Wh.astype(np.float64), to_host(W))
+        assert np.array_equal(Hh.astype(np.float64), to_host(H))
+        m.restart(77)
+        torch.cuda.synchronize()
+        W0, H0 = synth.starting_factors(77, pr.p, pr.n, pr.r)
+        assert np.array_equal(to_host(W), W0.astype(np.float64))
+        assert np.array_equal(to_host(H), H0.astype(np.float64))
+
+
+@pytest.mark.parametrize("max_iters,k", [(17, 5), (3, 8)])
+def test_device_loop_budget_poisson(max_iters, k):
+    """tol = 0: exactly max_iters iterations (rounds of k on the device, the
+    remainder on the host), equal to nmf_step."""
+    pr = synth.counts_problem(90, 140, 5, seed=17)
+    m, W, H = _ctx(pr)
+    with m:
+        done, L = m.converge(max_iters, tol=0.0, check_every=k)
+        Wc, Hc = to_host(W), to_host(H)
+    m2, W2, H2 = _ctx(pr)
+    with m2:
+        m2.step(max_iters)
+        L2 = m2.objective()
+    assert done == max_iters and L == L2
+    assert np.array_equal(Wc, to_host(W2)) and np.array_equal(Hc, to_host(H2))
