@@ -19,8 +19,9 @@
 //   k_pois_update  both factors in place from the segment partials (summed
 //                  in segment order), the sums and the old factors.
 // Both passes read V once each (float32, row-major, as the caller holds it);
-// b is formed twice (once per pass), so an iteration is 8pnr flops.  Every
-// sum runs in a fixed order: the result is deterministic.
+// b is formed twice (once per pass), so an iteration is 8pnr flops.  The
+// loglikelihood L is one more launch (k_pois_loglik).  Every sum runs in a
+// fixed order: the result is deterministic.
 #include <cstdint>
 #include <climits>
 
@@ -39,8 +40,9 @@ constexpr int kLW = kPT + 4;     // row stride of Wt and Qs (16-byte rows)
 // (H_J), Qs[64][kLW] (q of the tile, row-major).
 __host__ __device__ inline int pois_floats(int r) { return r * kLW + r * kPT + kPT * kLW; }
 
-// Row sums of H (which = 0: den of the W update) or column sums of W
-// (which = 1: den of the H update) for rank k = blockIdx.x / 2 ... in float64.
+// Block 2k + which: the row sum of H's rank k (which = 0, the denominator
+// of the W update) or the column sum of W's rank k (which = 1, of the H
+// update), in float64 (strided per thread, then a fixed tree).
 __global__ void k_pois_sums(const float* __restrict__ W, const float* __restrict__ H,
                             int64_t p, int64_t n, int r, double* __restrict__ sums) {
   __shared__ double red[kPThreads];
