@@ -165,6 +165,26 @@ nmf_status nmf_run(nmf_ctx* ctx, int max_iters, double tol, int check_every,
 nmf_status nmf_converge(nmf_ctx* ctx, int max_iters, double tol, int check_every,
                         int* iters_done, double* f_out);
 
+/* Quasi-Newton acceleration of the MM map (the scheme the paper names in
+ * Section 4; Zhou, Alexander & Lange).  Each iteration evaluates
+ * x1 = F(x_n) and x2 = F(x1) by two MM iterations (F = nmf_step(ctx, 1); x
+ * stacks W and H), keeps the secant pairs (x1 - x_n, x2 - x1) of the last q
+ * iterations as the columns of U and V (float32, on the device), forms
+ * U^T U and U^T V from float64 inner products in a fixed order, and takes
+ *     x_{n+1} = x1 + V (U^T U - U^T V)^-1 U^T (x1 - x_n)
+ * when all its entries are nonnegative and its objective is no worse than
+ * x2's, and x2 otherwise (also when the q x q system is singular), so an
+ * iteration never ends worse than two MM iterations.  Runs max_iters
+ * iterations or until Section 3's rule holds for tol on the model's
+ * objective (the Frobenius objective; L for the Poisson model, maximised).
+ * *iters_done, *f_out (the last objective) and *qn_taken (quasi-Newton
+ * points taken) are host memory; each may be NULL.  The workspace,
+ * (3 + 2q) (p + n) r floats, is allocated by the first call and sized for
+ * its q; later calls take any q up to that (NMF_EINVAL above it).
+ * 1 <= q <= 32.  Synchronises (three times per iteration).                  */
+nmf_status nmf_qn_run(nmf_ctx* ctx, int q, int max_iters, double tol, int* iters_done,
+                      double* f_out, int* qn_taken);
+
 /* Restart from Algorithm 1's seeded start on the same V (multiple random
  * starts): rebuild V's operand copies (one pass over V), draw W and H iid
  * uniform(0,1) from `seed` exactly as init_from_seed does, and re-form the

@@ -1,5 +1,6 @@
 // C ABI of the MM NMF library: contexts, workspaces, validation and the
 // per-iteration launch sequence.  See include/nmf.h for the contract.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -113,6 +114,19 @@ struct nmf_ctx {
   double* ppartW = nullptr;       // segW x p x r
   double* ppartH = nullptr;       // segH x n x r
   double* pobj_parts = nullptr;   // loglikelihood partials
+  // nmf_qn_run: the quasi-Newton workspace, made on first use for memory q
+  int qn_q = 0;
+  float* qn_x[3] = {nullptr, nullptr, nullptr};   // x_n, F(x_n), F(F(x_n))
+  float* qn_u = nullptr;              // q x N secant differences u
+  float* qn_v = nullptr;              // q x N secant differences v
+  double* qn_part = nullptr;          // 3q x chunks inner-product partials
+  double* qn_dot = nullptr;           // 3q inner products
+  double* qn_coef = nullptr;          // q coefficients
+  const float** qn_ptr = nullptr;     // device: 3q + 3q + q operand pointers
+  int* qn_neg = nullptr;              // sign flag of the quasi-Newton point
+  double* qn_hdot = nullptr;          // pinned mirrors: 3q dots, then q coefficients
+  const float** qn_hptr = nullptr;    // pinned: 7q pointers
+  int* qn_hneg = nullptr;             // pinned
   // nmf_converge: the run's device state and the graph of its loop, built
   // for one check interval and kept until another is asked for
   RunState* run_dev = nullptr;
@@ -153,8 +167,6 @@ nmf_status dalloc(nmf_ctx* c, void** p, size_t bytes) {
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
   return NMF_OK;
 }
-
-bool is_aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 cudaEvent_t take_event(nmf_ctx* c) {
   if (!c->ev_pool.empty()) {
@@ -433,6 +445,9 @@ void free_ctx(nmf_ctx* c) {
   if (c->f_host) cudaFreeHost(c->f_host);
   if (c->err_host) cudaFreeHost(c->err_host);
   if (c->run_host) cudaFreeHost(c->run_host);
+  if (c->qn_hdot) cudaFreeHost(c->qn_hdot);
+  if (c->qn_hptr) cudaFreeHost((void*)c->qn_hptr);
+  if (c->qn_hneg) cudaFreeHost(c->qn_hneg);
   if (c->conv_exec) cudaGraphExecDestroy(c->conv_exec);
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
   for (auto& it : c->ev_open) { cudaEventDestroy(it.a); cudaEventDestroy(it.b); }
@@ -715,7 +730,202 @@ nmf_status nmf_converge(nmf_ctx* c, int max_iters, double tol, int check_every,
   return NMF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The factor operand planes from the factors as they are now (after the
+// quasi-Newton loop wrote W and H itself).
+nmf_status refresh_planes(nmf_ctx* c) {
+  if (c->pois) return NMF_OK;
+  CK(launch_factor_planes(c->W, kFactorRowMajor, c->p, c->r, c->r, c->Wop_hi, c->Wop_lo,
+                          c->ld_p, c->plane, c->st), "W planes");
+  CK(launch_factor_planes(c->H, kFactorColMajor, c->n, c->n, c->r, c->Hop_hi, c->Hop_lo,
+                          c->ld_n, c->plane, c->st), "H planes");
+  launched(2);
+  return NMF_OK;
+}
+
+// x <- (W, H) and (W, H) <- x, x stacking W (p r entries) then H.
+nmf_status save_state(nmf_ctx* c, float* x) {
+  const size_t nw = (size_t)c->p * c->r, nh = (size_t)c->r * c->n;
+  CK(cudaMemcpyAsync(x, c->W, nw * 4, cudaMemcpyDeviceToDevice, c->st), "copy W");
+  CK(cudaMemcpyAsync(x + nw, c->H, nh * 4, cudaMemcpyDeviceToDevice, c->st), "copy H");
+  return NMF_OK;
+}
+nmf_status load_state(nmf_ctx* c, const float* x) {
+  const size_t nw = (size_t)c->p * c->r, nh = (size_t)c->r * c->n;
+  CK(cudaMemcpyAsync(c->W, x, nw * 4, cudaMemcpyDeviceToDevice, c->st), "copy W");
+  CK(cudaMemcpyAsync(c->H, x + nw, nh * 4, cudaMemcpyDeviceToDevice, c->st), "copy H");
+  return refresh_planes(c);
+}
+
+nmf_status qn_workspace(nmf_ctx* c, int q) {
+  if (c->qn_q >= q) return NMF_OK;
+  if (c->qn_q != 0) {
+    set_err(&c->err, "the quasi-Newton workspace of a context is sized by its first call "
+            "(q <= %d)", c->qn_q);
+    return NMF_EINVAL;
+  }
+  const int64_t N = (c->p + c->n) * (int64_t)c->r;
+  nmf_status s;
+  for (int i = 0; i < 3; ++i)
+    if ((s = dalloc(c, (void**)&c->qn_x[i], (size_t)N * 4)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->qn_u, (size_t)q * N * 4)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->qn_v, (size_t)q * N * 4)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->qn_part, (size_t)3 * q * qn_dot_chunks(N) * 8)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->qn_dot, (size_t)3 * q * 8)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->qn_coef, (size_t)q * 8)) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->qn_ptr, (size_t)7 * q * sizeof(void*))) != NMF_OK) return s;
+  if ((s = dalloc(c, (void**)&c->qn_neg, sizeof(int))) != NMF_OK) return s;
+  CK(cudaMallocHost((void**)&c->qn_hdot, (size_t)4 * q * 8), "cudaMallocHost");
+  CK(cudaMallocHost((void**)&c->qn_hptr, (size_t)7 * q * sizeof(void*)), "cudaMallocHost");
+  CK(cudaMallocHost((void**)&c->qn_hneg, sizeof(int)), "cudaMallocHost");
+  c->qn_q = q;
+  return NMF_OK;
+}
+
+// Solves A c = b (m x m, row-major, float64) by Gaussian elimination with
+// partial pivoting; false if a pivot is below 1e-13 of A's largest entry.
+bool solve_small(std::vector<double> A, std::vector<double> b, int m, std::vector<double>* x) {
+  double amax = 0.0;
+  for (double v : A) amax = std::max(amax, std::fabs(v));
+  if (!(amax > 0.0) || !std::isfinite(amax)) return false;
+  for (int k = 0; k < m; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < m; ++i)
+      if (std::fabs(A[i * m + k]) > std::fabs(A[piv * m + k])) piv = i;
+    if (!(std::fabs(A[piv * m + k]) > 1e-13 * amax)) return false;
+    if (piv != k) {
+      for (int j = 0; j < m; ++j) std::swap(A[k * m + j], A[piv * m + j]);
+      std::swap(b[k], b[piv]);
+    }
+    for (int i = k + 1; i < m; ++i) {
+      const double f = A[i * m + k] / A[k * m + k];
+      for (int j = k; j < m; ++j) A[i * m + j] -= f * A[k * m + j];
+      b[i] -= f * b[k];
+    }
+  }
+  x->assign(m, 0.0);
+  for (int i = m - 1; i >= 0; --i) {
+    double t = b[i];
+    for (int j = i + 1; j < m; ++j) t -= A[i * m + j] * (*x)[j];
+    (*x)[i] = t / A[i * m + i];
+    if (!std::isfinite((*x)[i])) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+nmf_status nmf_qn_run(nmf_ctx* c, int q, int max_iters, double tol, int* iters_done,
+                      double* f_out, int* qn_taken) {
+  if (!c) { set_err(nullptr, "ctx is NULL"); return NMF_EINVAL; }
+  if (q < 1 || q > 32 || max_iters < 0 || !(tol >= 0.0)) {
+    set_err(&c->err, "need 1 <= q <= 32, max_iters >= 0, tol >= 0");
+    return NMF_EINVAL;
+  }
+  nmf_status s = qn_workspace(c, q);
+  if (s != NMF_OK) return s;
+  const int64_t nw = (int64_t)c->p * c->r;
+  const int64_t N = nw + (int64_t)c->r * c->n;
+  const double sign = c->pois ? -1.0 : 1.0;   // the quantity minimised
+  float* X0 = c->qn_x[0];
+  float* X1 = c->qn_x[1];
+  float* X2 = c->qn_x[2];
+  std::vector<double> UU((size_t)q * q, 0.0), UV((size_t)q * q, 0.0);
+  double f = 0.0;
+  if ((s = nmf_objective(c, &f)) != NMF_OK) return s;
+  double g = sign * f;
+  int done = 0, taken = 0;
+  for (int it = 0; it < max_iters; ++it) {
+    // the secant pair of this iterate: x_n, F(x_n), F(F(x_n))
+    if ((s = save_state(c, X0)) != NMF_OK) return s;
+    if ((s = nmf_step(c, 1)) != NMF_OK) return s;
+    if ((s = save_state(c, X1)) != NMF_OK) return s;
+    if ((s = nmf_step(c, 1)) != NMF_OK) return s;
+    if ((s = save_state(c, X2)) != NMF_OK) return s;
+    const int slot = it % q;
+    float* us = c->qn_u + (int64_t)slot * N;
+    float* vs = c->qn_v + (int64_t)slot * N;
+    CK(qn_secant(us, vs, X0, X1, X2, N, c->st), "secant");
+    launched(1);
+    // inner products of the new pair with the memory (oldest first)
+    const int m = it + 1 < q ? it + 1 : q;
+    std::vector<int> act(m);
+    for (int a = 0; a < m; ++a) act[a] = (it - m + 1 + a) % q;
+    const float** hp = c->qn_hptr;
+    for (int a = 0; a < m; ++a) {
+      const float* uj = c->qn_u + (int64_t)act[a] * N;
+      const float* vj = c->qn_v + (int64_t)act[a] * N;
+      hp[3 * a + 0] = uj; hp[3 * q + 3 * a + 0] = us;   // <u_j, u_new>
+      hp[3 * a + 1] = uj; hp[3 * q + 3 * a + 1] = vs;   // <u_j, v_new>
+      hp[3 * a + 2] = us; hp[3 * q + 3 * a + 2] = vj;   // <u_new, v_j>
+    }
+    CK(cudaMemcpyAsync(c->qn_ptr, hp, (size_t)6 * q * sizeof(void*), cudaMemcpyHostToDevice,
+                       c->st), "copy pointers");
+    CK(qn_dots(c->qn_ptr, c->qn_ptr + 3 * q, 3 * m, N, c->qn_part, c->qn_dot, c->st), "dots");
+    launched(2);
+    CK(cudaMemcpyAsync(c->qn_hdot, c->qn_dot, (size_t)3 * m * 8, cudaMemcpyDeviceToHost, c->st),
+       "copy dots");
+    double f2 = 0.0;   // synchronises: the dots are in qn_hdot too
+    if ((s = nmf_objective(c, &f2)) != NMF_OK) return s;
+    const double g2 = sign * f2;
+    for (int a = 0; a < m; ++a) {
+      const int j = act[a];
+      UU[(size_t)j * q + slot] = UU[(size_t)slot * q + j] = c->qn_hdot[3 * a + 0];
+      UV[(size_t)j * q + slot] = c->qn_hdot[3 * a + 1];
+      UV[(size_t)slot * q + j] = c->qn_hdot[3 * a + 2];
+    }
+    // (U^T U - U^T V) coef = U^T u_new over the active pairs
+    std::vector<double> A((size_t)m * m), rhs(m), coef;
+    for (int a = 0; a < m; ++a) {
+      for (int b = 0; b < m; ++b)
+        A[(size_t)a * m + b] = UU[(size_t)act[a] * q + act[b]] - UV[(size_t)act[a] * q + act[b]];
+      rhs[a] = UU[(size_t)act[a] * q + slot];
+    }
+    double gnew = g2;
+    if (solve_small(A, rhs, m, &coef)) {
+      for (int a = 0; a < m; ++a) c->qn_hdot[3 * q + a] = coef[a];
+      const float** hv = c->qn_hptr + 6 * q;
+      for (int a = 0; a < m; ++a) hv[a] = c->qn_v + (int64_t)act[a] * N;
+      *c->qn_hneg = 0;
+      CK(cudaMemcpyAsync(c->qn_coef, c->qn_hdot + 3 * q, (size_t)m * 8, cudaMemcpyHostToDevice,
+                         c->st), "copy coefficients");
+      CK(cudaMemcpyAsync(c->qn_ptr + 6 * q, hv, (size_t)m * sizeof(void*),
+                         cudaMemcpyHostToDevice, c->st), "copy pointers");
+      CK(cudaMemsetAsync(c->qn_neg, 0, sizeof(int), c->st), "memset");
+      CK(qn_combine(c->W, c->H, nw, N, X1, c->qn_ptr + 6 * q, c->qn_coef, m, c->qn_neg, c->st),
+         "combine");
+      launched(1);
+      CK(cudaMemcpyAsync(c->qn_hneg, c->qn_neg, sizeof(int), cudaMemcpyDeviceToHost, c->st),
+         "copy flag");
+      CK(cudaStreamSynchronize(c->st), "sync");
+      bool take = false;
+      if (*c->qn_hneg == 0) {
+        if ((s = refresh_planes(c)) != NMF_OK) return s;
+        double fq = 0.0;
+        if ((s = nmf_objective(c, &fq)) != NMF_OK) return s;
+        if (sign * fq <= g2) { take = true; gnew = sign * fq; }
+      }
+      if (take) ++taken;
+      else if ((s = load_state(c, X2)) != NMF_OK) return s;
+    }
+    ++done;
+    const double gprev = g;
+    g = gnew;
+    if (tol > 0.0 && std::fabs(g - gprev) / (std::fabs(gprev) + 1.0) < tol) break;
+  }
+  if (iters_done) *iters_done = done;
+  if (f_out) *f_out = sign * g;
+  if (qn_taken) *qn_taken = taken;
+  return check_device_error(c);
+}
+
 nmf_status nmf_read_gram(nmf_ctx* c, int which, double* out) {
+
   if (!c || !out || (which != 0 && which != 1)) {
     set_err(c ? &c->err : nullptr, "bad argument to nmf_read_gram");
     return NMF_EINVAL;

@@ -48,7 +48,7 @@ EXPORTS = [
     "nmf_batched_step", "nmf_batched_objective", "nmf_batched_destroy",
     "nmf_status_str", "nmf_last_error", "nmf_version", "nmf_restart",
     "nmf_kernel_launches", "nmf_profile_enable", "nmf_profile_read", "nmf_gram_noalloc",
-    "nmf_selfcheck_div", "nmf_test_expire_next_wait", "nmf_converge",
+    "nmf_selfcheck_div", "nmf_test_expire_next_wait", "nmf_converge", "nmf_qn_run",
 ]
 
 _lib = None
@@ -77,6 +77,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "nmf_converge": ([c_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)],
                          ctypes.c_int),
+        "nmf_qn_run": ([c_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                        ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "nmf_read_gram": ([c_p, ctypes.c_int, c_p], ctypes.c_int),
         "nmf_solve": ([cfgp, c_p, c_p, c_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), c_p],
                       ctypes.c_int),
@@ -212,6 +215,15 @@ class NMF:
         _check(self.lib.nmf_converge(self.ctx, int(max_iters), float(tol), int(check_every),
                                      ctypes.byref(done), ctypes.byref(f)), self.ctx)
         return done.value, f.value
+
+    def qn_run(self, q: int, max_iters: int, tol: float = 0.0):
+        """Quasi-Newton acceleration with memory q (see nmf_qn_run).
+        Returns (iterations, objective, quasi-Newton points taken)."""
+        done, f, taken = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+        _check(self.lib.nmf_qn_run(self.ctx, int(q), int(max_iters), float(tol),
+                                   ctypes.byref(done), ctypes.byref(f), ctypes.byref(taken)),
+               self.ctx)
+        return done.value, f.value, taken.value
 
     def expire_next_wait(self):
         """Test hook: the next half step's grid-wide waits run out (about
