@@ -185,16 +185,23 @@ def algorithmic(prec, p, n, r):
     return bytes_, flops
 
 
-TC_SOURCES = ["k_stream_tc.cu", "tc_epi.cuh", "tc_ptx.cuh", "epilogue.cuh", "tc.cuh",
-              "nmf_internal.cuh"]
+# The device code of each kernel whose DRAM traffic is recorded: its own
+# translation unit and the headers with device code it includes (host-only
+# declarations, nmf_internal.cuh, are left out: they change no kernel).
+KERNEL_SOURCES = {
+    "k_stream_tc": ["k_stream_tc.cu", "tc_epi.cuh", "tc_ptx.cuh", "epilogue.cuh", "tc.cuh",
+                    "nmf_device.cuh"],
+    "k_stream_f32": ["k_stream_f32.cu", "tc_epi.cuh", "tc_ptx.cuh", "epilogue.cuh", "tc.cuh",
+                     "nmf_device.cuh"],
+}
 
 
-def kernel_source_digest():
-    """sha256 over the tensor-core kernel's sources: a recorded ncu traffic
-    figure is used only while the kernel is unchanged since its capture."""
+def kernel_source_digest(kernel="k_stream_tc"):
+    """sha256 over one kernel's device sources: a recorded ncu traffic figure
+    is used only while the kernel is unchanged since its capture."""
     import hashlib
     h = hashlib.sha256()
-    for f in TC_SOURCES:
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_1003_3272_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -211,7 +218,8 @@ def read_traffic(kernel_key):
             d = json.load(fh).get(kernel_key)
     except (OSError, ValueError):
         return None
-    if not d or d.get("kernel_digest") != kernel_source_digest():
+    kernel = kernel_key.split("/")[0]
+    if not d or kernel not in KERNEL_SOURCES or d.get("kernel_digest") != kernel_source_digest(kernel):
         return None
     return d.get("traffic_bytes_per_launch")
 
@@ -232,15 +240,17 @@ def make_problem(args):
     return pr, pr.name, "synthetic (seeded iid Exponential(1); no dataset)"
 
 
-def time_planted(pr, prec, steps, warmup, ws, local, sample_clocks=False, profile=True):
+def time_planted(pr, prec, steps, warmup, ws, local, sample_clocks=False, profile=True,
+                 V_dev=None):
     """Time `steps` benchmark steps of one precision on problem `pr` (the
     planted problem unless --workload says otherwise).  Returns the
-    measurement dict (updates/s, per-launch stream time, ...)."""
+    measurement dict (updates/s, per-launch stream time, ...).  `V_dev`: V
+    already on the device (else it is copied from pr.V)."""
     import torch
     from paper_1003_3272_gb300 import nmf
     p, n, r, iters = pr.p, pr.n, pr.r, pr.iters
     seed = pr.seed
-    V = torch.from_numpy(pr.V).cuda()
+    V = V_dev if V_dev is not None else torch.from_numpy(pr.V).cuda()
     W = torch.empty(p, r, device="cuda")
     H = torch.empty(r, n, device="cuda")
     stream = torch.cuda.current_stream()
@@ -458,6 +468,58 @@ def time_converge(ws, prec="fp32", tol=1e-9, max_iters=100000):
                                       and np.array_equal(a[3], b[3]))}
 
 
+def time_workloads(ws, local, clocks, tall_ranks=(16, 32, 64, 128)):
+    """The other measured workloads, one timed step each (restart + the
+    workload's iterations + objective, after one warm-up step), V generated
+    once per workload and kept on the device across the forms:
+      faces 361 x 2429, r = 10, 50 iterations, all four forms (L2-resident,
+            launch-bound: absolute time);
+      tall 65536 x 4096, r in {16, 32, 64, 128}, 20 iterations, all four forms;
+      large 131072 x 16384, r = 64, 20 iterations, FP32 and BF16x3.
+    Each entry: updates/s, the roofline of its dominant kernel (CUDA-event
+    average of the streaming launches) and the relative objective error
+    against the stored float64 oracle trajectory."""
+    import dataclasses
+    import torch
+    from paper_1003_3272_gb300 import synth
+    out = {}
+
+    def run(pr, precs, wname):
+        V = torch.from_numpy(pr.V).cuda()
+        ent, objs = {}, {}
+        for prec in precs:
+            res = time_planted(pr, prec, 1, 1, ws, local, V_dev=V)
+            rf = roofline(prec, pr.p, pr.n, pr.r, res, clocks, wname)
+            objs[prec] = res["objective"]
+            ent[prec] = {"updates_per_s": round(res["value"], 1),
+                         "ms_per_step": round(res["ms"], 3),
+                         "roofline": {k: rf[k] for k in ("bound", "achieved", "peak", "unit",
+                                                         "frac", "avg_launch_us", "kernel",
+                                                         "traffic")}}
+        acc = accuracy(wname, pr.iters, objs)
+        for prec in precs:
+            e = acc.get("rel_objective_error_vs_fp64_oracle")
+            ent[prec]["rel_objective_error_vs_fp64_oracle"] = e.get(prec) if e else None
+        ent["iterations"] = pr.iters
+        del V
+        torch.cuda.empty_cache()
+        return ent
+
+    all4 = ["fp32", "tf32", "bf16x3", "bf16"]
+    pr = synth.faces()
+    out[pr.name] = run(pr, all4, pr.name)
+    base = synth.tall(tall_ranks[0])
+    for r in tall_ranks:
+        W0, H0 = synth.starting_factors(base.seed, base.p, base.n, r)
+        pr = dataclasses.replace(base, W0=W0, H0=H0, r=r, name=f"{synth.TALL['name']}_r{r}")
+        out[pr.name] = run(pr, all4, pr.name)
+    del base, pr
+    pr = synth.large()
+    out[pr.name] = run(pr, ["fp32", "bf16x3"], pr.name)
+    del pr
+    return out
+
+
 def oracle_objective(workload, iters):
     """The float64 oracle's objective after `iters` iterations from the seeded
     start on `workload`, as stored in tests/golden/objectives.json (written by
@@ -597,37 +659,81 @@ def run_gpu(args, ws, rank, local):
             out["batched"] = time_batched("bf16x3", max(2, args.steps // 2), 2, 20, ws)
             out["converge"] = time_converge(ws)
             out["poisson"] = time_poisson(ws, clocks)
+            if not args.no_workloads:
+                out["by_workload"] = time_workloads(ws, local, clocks)
     else:
         out["accuracy"] = accuracy(wname, iters, {args.prec: main["objective"]})
     return out, pr
 
 
-def cpu_baseline(pr, budget_s):
-    """The FP64 oracle as it stands, timed on this host's cores on a bounded
-    sample of the same workload: MM iterations of the full problem."""
+def oracle_iterations(V, W0, H0, eps, budget_s):
+    """MM iterations of the float64 oracle as it stands until `budget_s`
+    seconds have passed (at least 2, after one warm-up): (count, seconds)."""
     import numpy as np
+    from oracle import nmf_oracle as orc
+    W = W0.astype(np.float64)
+    H = H0.astype(np.float64)
+    orc.step(V, W, H, eps)  # warm BLAS
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        W, H = orc.step(V, W, H, eps)
+        k += 1
+        if time.perf_counter() - t0 > budget_s and k >= 2:
+            break
+    return k, time.perf_counter() - t0
+
+
+SINGLE_THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1",
+                     "MKL_NUM_THREADS": "1", "BLIS_NUM_THREADS": "1",
+                     "VECLIB_MAXIMUM_THREADS": "1", "NUMEXPR_NUM_THREADS": "1"}
+
+
+def _single_thread_leg(pr, budget_s):
+    """The same oracle iterations in a child interpreter whose BLAS runs one
+    thread (the paper's one-core CPU protocol); V, W0, H0 pass through a
+    temporary .npz file.  The child is a fresh process (fork + exec), so it
+    shares no CUDA state with this one."""
+    import tempfile
+    import numpy as np
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "prob.npz")
+        np.savez(path, V=pr.V, W0=pr.W0, H0=pr.H0)
+        code = ("import json, sys, numpy as np; sys.path.insert(0, %r); import bench; "
+                "z = np.load(%r); k, dt = bench.oracle_iterations(z['V'], z['W0'], z['H0'], "
+                "%r, %r); print(json.dumps([k, dt]))" % (ROOT, path, pr.eps, budget_s))
+        env = dict(os.environ, **SINGLE_THREAD_ENV)
+        try:
+            res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                                 env=env, timeout=budget_s * 10 + 120)
+            k, dt = json.loads(res.stdout.strip().splitlines()[-1])
+        except (subprocess.SubprocessError, ValueError, IndexError, OSError) as e:
+            return {"value": None, "unit": "updates/s", "cores": 1, "kind": "oracle",
+                    "sample": f"not run: {type(e).__name__}"}
+    return {"value": round(k / dt, 4), "unit": "updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{k} MM iterations of the {pr.p}x{pr.n} r={pr.r} {pr.name} problem "
+                      f"in float64 numpy/BLAS on one thread ({', '.join(sorted(SINGLE_THREAD_ENV))}"
+                      f" = 1), {dt:.1f} s"}
+
+
+def cpu_baseline(pr, budget_s, single_thread=True):
+    """The FP64 oracle as it stands, timed on this host's cores on a bounded
+    sample of the same workload: MM iterations of the full problem, once with
+    BLAS on all cores (value, cores) and once on one thread (single_thread),
+    as the paper timed its CPU baseline on one core."""
     if pr.V.size > (1 << 29):
         return {"value": None, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle",
                 "sample": "not run: the oracle widens V to float64 for every product "
                           f"({pr.V.size * 8 / 1e9:.0f} GB per copy); the sampled parity "
                           "tests cover this workload"}
-    from oracle import nmf_oracle as orc
-    V = pr.V
-    W = pr.W0.astype(np.float64)
-    H = pr.H0.astype(np.float64)
-    orc.step(V, W, H, pr.eps)  # warm BLAS
-    t0 = time.perf_counter()
-    k = 0
-    while True:
-        W, H = orc.step(V, W, H, pr.eps)
-        k += 1
-        if time.perf_counter() - t0 > budget_s and k >= 2:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": round(k / dt, 4), "unit": "updates/s", "cores": os.cpu_count(),
-            "kind": "oracle",
-            "sample": f"{k} MM iterations (H then W update) of the {pr.p}x{pr.n} r={pr.r} "
-                      f"{pr.name} problem in float64 numpy/BLAS, {dt:.1f} s"}
+    k, dt = oracle_iterations(pr.V, pr.W0, pr.H0, pr.eps, budget_s)
+    out = {"value": round(k / dt, 4), "unit": "updates/s", "cores": os.cpu_count(),
+           "kind": "oracle",
+           "sample": f"{k} MM iterations (H then W update) of the {pr.p}x{pr.n} r={pr.r} "
+                     f"{pr.name} problem in float64 numpy/BLAS on all cores, {dt:.1f} s"}
+    if single_thread:
+        out["single_thread"] = _single_thread_leg(pr, budget_s)
+    return out
 
 
 def run_reference_batched(args):
@@ -717,6 +823,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other precisions, the batched workload and the accuracy check")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the by_workload block (faces, tall sweep, large)")
     args = ap.parse_args()
 
     if args.impl == "reference":

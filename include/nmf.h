@@ -231,7 +231,11 @@ void nmf_batched_destroy(nmf_batch* b);
  * It allocates nothing: its scratch is a static 8 MiB device array inside
  * the library, held by every GPU that loads the library until exit.  The
  * first call on a device (with that device current) looks the array's
- * device address up; make that first call before any stream capture.
+ * device address up; under CUDA's lazy module loading that lookup may load
+ * the library's device code on the device, which can allocate and
+ * synchronise inside the driver, so make the first call per device at
+ * start-up, off any latency-critical path and before any stream capture.
+ * A failed lookup (NMF_ECUDA) is not remembered: the next call retries.
  * Sizes needing more than 2^21 floats of scratch (ceil(M/128)*r*r + r*r)
  * are rejected with NMF_EINVAL and a message in nmf_last_error(NULL).  All
  * calls share the scratch: calls that overlap on the GPU race and must not

@@ -56,7 +56,8 @@ __global__ void k_qn_dot_sum(const double* __restrict__ part, int chunks, int nd
 }
 
 // x = x1 + sum_j coef[j] V_j in float64, rounded once to float32, written to
-// W (entries [0, nw)) and H (the rest); *neg = 1 if an entry is negative.
+// W (entries [0, nw)) and H (the rest); *neg = 1 if an entry is negative or
+// not finite (NaN fails the x >= 0 test), so such a point is never taken.
 __global__ void k_qn_combine(float* __restrict__ W, float* __restrict__ H, int64_t nw, int64_t N,
                              const float* __restrict__ x1, const float* const* __restrict__ Vj,
                              const double* __restrict__ coef, int m, int* __restrict__ neg) {
@@ -65,7 +66,7 @@ __global__ void k_qn_combine(float* __restrict__ W, float* __restrict__ H, int64
     double x = (double)x1[i];
     for (int j = 0; j < m; ++j) x = fma(coef[j], (double)Vj[j][i], x);
     const float xf = (float)x;
-    if (xf < 0.f) atomicExch(neg, 1);
+    if (!(xf >= 0.f) || isinf(xf)) atomicExch(neg, 1);
     if (i < nw) W[i] = xf;
     else H[i - nw] = xf;
   }

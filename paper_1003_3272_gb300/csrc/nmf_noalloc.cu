@@ -12,8 +12,13 @@
 // The array's name is a host-side stand-in in host code, not a device
 // address, so its device address is looked up once per device with
 // cudaGetSymbolAddress (on the first call made with that device current)
-// and then passed to the kernels.  Every GPU that loads the library holds
-// the array until the process exits.  All calls share it and it keeps the
+// and then passed to the kernels.  Only a successful lookup is kept: after a
+// failed one the next call tries again.  With CUDA's lazy module loading the
+// library's device code, and the array with it, may be loaded on a device
+// only at that first lookup, which can then allocate and synchronise inside
+// the driver; so the first call per device belongs off the latency-critical
+// path (at start-up, before any stream capture).  From then on the device
+// holds the array until the process exits.  All calls share it and it keeps the
 // last call's contents; the kernels overwrite every entry they later read,
 // so nothing needs clearing.  Calls that overlap on the GPU (different
 // streams, or different host threads) race on the array and must not be
@@ -30,9 +35,8 @@ constexpr size_t kScratchFloats = size_t(1) << 21;
 static __device__ __align__(256) float g_scratch[kScratchFloats];
 
 constexpr int kMaxDevices = 64;
-float* g_scratch_ptr[kMaxDevices];
-cudaError_t g_setup_status[kMaxDevices];
-std::once_flag g_setup_once[kMaxDevices];
+float* g_scratch_ptr[kMaxDevices];   // device address per device, once found
+std::mutex g_setup_mu;
 
 char* msg_buf() {
   static thread_local char buf[256];
@@ -77,15 +81,21 @@ nmf_status nmf_gram_noalloc(const float* F, int32_t layout, int64_t M, int64_t l
   if (dev < 0 || dev >= kMaxDevices) {
     return fail(NMF_EUNSUPPORTED, "nmf_gram_noalloc: device ordinal beyond 63");
   }
-  std::call_once(g_setup_once[dev], [dev] {
-    g_setup_status[dev] = cudaGetSymbolAddress((void**)&g_scratch_ptr[dev], g_scratch);
-  });
-  if (g_setup_status[dev] != cudaSuccess) {
-    snprintf(msg_buf(), 256, "nmf_gram_noalloc: cudaGetSymbolAddress: %s",
-             cudaGetErrorString(g_setup_status[dev]));
-    return fail(NMF_ECUDA, msg_buf());
+  float* part = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    if (!g_scratch_ptr[dev]) {
+      float* p = nullptr;
+      e = cudaGetSymbolAddress((void**)&p, g_scratch);
+      if (e != cudaSuccess || !p) {
+        snprintf(msg_buf(), 256, "nmf_gram_noalloc: cudaGetSymbolAddress: %s",
+                 cudaGetErrorString(e));
+        return fail(NMF_ECUDA, msg_buf());
+      }
+      g_scratch_ptr[dev] = p;
+    }
+    part = g_scratch_ptr[dev];
   }
-  float* part = g_scratch_ptr[dev];
   float* G32 = part + tiles * r * r;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if ((e = launch_gram_tiles(F, layout == 0 ? kFactorRowMajor : kFactorColMajor, M, ldf, r, part,

@@ -41,10 +41,12 @@ def _oracle_maps(pr, model="gaussian"):
     return F, g, x0, unpack
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
-def test_first_iteration_matches_oracle(prec):
+@pytest.mark.parametrize("prec,bar", [("fp32", 1e-4), ("bf16x3", 2e-3)])
+def test_first_iteration_matches_oracle(prec, bar):
     """One iteration with memory 1: the secant pair, the scalar system and
-    the quasi-Newton point (or its fallback) as the oracle takes them."""
+    the quasi-Newton point (or its fallback) as the oracle takes them; the
+    float32 form at the FP32 iterate bar (1e-4 per entry), the split-bf16
+    form at its own (the products carry 2^-17 relative operand error)."""
     pr = synth.uniform_problem(60, 80, 4, seed=21)
     m, W, H = _ctx(pr, prec=prec)
     with m:
@@ -54,7 +56,7 @@ def test_first_iteration_matches_oracle(prec):
     x, gs, acc = qn.qn_run(F, g, x0, 1, 1)
     Wo, Ho = unpack(x)
     assert done == 1 and taken == acc
-    assert entry_rel_err(Wg, Wo)[0] < 2e-3 and entry_rel_err(Hg, Ho)[0] < 2e-3
+    assert entry_rel_err(Wg, Wo)[0] < bar and entry_rel_err(Hg, Ho)[0] < bar
     assert abs(f - gs[-1]) <= 1e-4 * gs[-1]
 
 
