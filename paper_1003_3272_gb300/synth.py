@@ -55,6 +55,7 @@ STREAM_HSTAR = 4
 STREAM_NOISE = 5
 STREAM_SHAPES = 6
 STREAM_COUNTS = 7
+STREAM_PET_COUNTS = 8
 
 BASE_SEED = 20100316
 
@@ -311,3 +312,153 @@ def batch(count: int = 512, seed: int = BASE_SEED + 3, iters: int = 100,
 def counts(seed: int = BASE_SEED + 5, iters: int = 20) -> Problem:
     c = COUNTS
     return counts_problem(c["p"], c["n"], c["r"], seed, 5.0, iters, c["name"])
+
+
+# ----------------------------------------------------------------------------
+# PET reconstruction inputs (Section 3.2): detector geometry, phantom, counts
+# ----------------------------------------------------------------------------
+#
+# A G x G grid of unit pixels fills the square [0, G]^2 (pixel j = row * G +
+# col covers [col, col+1] x [row, row+1]); `ndet` detectors sit evenly on a
+# circle around it (angles 2 pi (a + 1/2) / ndet, radius a little beyond the
+# grid's half diagonal), and every unordered pair of detectors is one line of
+# flight, so d = ndet (ndet - 1) / 2 (64 detectors give the 2016 lines of the
+# paper's 64 x 64 example).  The geometry constant e_ij is the length of line
+# i inside pixel j, computed exactly from the line's crossings of the grid
+# lines (Siddon, Med. Phys. 12, 1985).  This is the stand-in for the
+# simulated scanner of the paper's example; the method's own first step, the
+# scaling of E to unit column sums, is not done here.
+
+def pet_system_matrix(grid: int, ndet: int) -> np.ndarray:
+    """E (d x p, float32, row-major): intersection lengths of the ndet
+    (ndet - 1) / 2 detector-pair lines with the grid x grid unit pixels."""
+    G = int(grid)
+    c = G / 2.0
+    R = 0.5 * math.sqrt(2.0) * G + 1.0
+    ang = 2.0 * math.pi * (np.arange(ndet) + 0.5) / ndet
+    det = np.stack([c + R * np.cos(ang), c + R * np.sin(ang)], axis=1)
+    ia, ib = np.triu_indices(ndet, 1)
+    P0, D = det[ia], det[ib] - det[ia]
+    length = np.hypot(D[:, 0], D[:, 1])
+    planes = np.arange(G + 1, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tx = (planes[None, :] - P0[:, :1]) / D[:, :1]
+        ty = (planes[None, :] - P0[:, 1:]) / D[:, 1:]
+    tx[~np.isfinite(tx)] = np.nan
+    ty[~np.isfinite(ty)] = np.nan
+    # the part of each line inside the box [0, G]^2
+    lo = np.fmax(np.fmin(tx[:, 0], tx[:, -1]), np.fmin(ty[:, 0], ty[:, -1]))
+    hi = np.fmin(np.fmax(tx[:, 0], tx[:, -1]), np.fmax(ty[:, 0], ty[:, -1]))
+    lo = np.nan_to_num(np.fmax(lo, 0.0), nan=0.0)
+    hi = np.nan_to_num(np.fmin(hi, 1.0), nan=0.0)
+    t = np.concatenate([tx, ty, lo[:, None], hi[:, None]], axis=1)
+    t = np.where((t >= lo[:, None]) & (t <= hi[:, None]), t, np.nan)
+    t.sort(axis=1)                                  # NaNs sort last
+    dt = t[:, 1:] - t[:, :-1]
+    mid = 0.5 * (t[:, 1:] + t[:, :-1])
+    x = P0[:, :1] + mid * D[:, :1]
+    y = P0[:, 1:] + mid * D[:, 1:]
+    ok = np.isfinite(dt) & (dt > 0)
+    col = np.floor(np.where(ok, x, -1)).astype(np.int64)
+    row = np.floor(np.where(ok, y, -1)).astype(np.int64)
+    ok &= (col >= 0) & (col < G) & (row >= 0) & (row < G)
+    d = len(ia)
+    E = np.zeros((d, G * G), dtype=np.float64)
+    li = np.broadcast_to(np.arange(d)[:, None], ok.shape)[ok]
+    np.add.at(E, (li, (row * G + col)[ok]), (dt * length[:, None])[ok])
+    return E.astype(np.float32)
+
+
+def pet_phantom(grid: int) -> np.ndarray:
+    """True intensities (p, float64) of a synthetic emission image: a
+    background disk with brighter and darker elliptical inserts, on the
+    grid's pixel centres (relative units; pet_problem scales them)."""
+    G = int(grid)
+    u = (np.arange(G) + 0.5) / G * 2.0 - 1.0             # pixel centres in [-1, 1]
+    X, Y = np.meshgrid(u, u)                              # X: column, Y: row
+    img = np.zeros((G, G))
+    # (centre x, centre y, semi-axis a, semi-axis b, rotation, added intensity)
+    for cx, cy, a, b, th, val in [
+            (0.0, 0.0, 0.85, 0.80, 0.0, 1.0),
+            (-0.30, 0.15, 0.22, 0.35, 0.4, 2.0),
+            (0.35, 0.25, 0.18, 0.12, -0.3, 3.0),
+            (0.10, -0.45, 0.30, 0.10, 0.0, -0.6),
+            (-0.20, -0.20, 0.08, 0.08, 0.0, 4.0),
+            (0.45, -0.10, 0.06, 0.15, 0.8, 2.5)]:
+        xr = (X - cx) * math.cos(th) + (Y - cy) * math.sin(th)
+        yr = -(X - cx) * math.sin(th) + (Y - cy) * math.cos(th)
+        img[(xr / a) ** 2 + (yr / b) ** 2 <= 1.0] += val
+    return img.reshape(-1)
+
+
+def grid_neighbours(grid: int):
+    """The neighbourhood system N of the penalty (Section 3.2): first-order
+    (horizontal and vertical) adjacency on the grid, as CSR arrays
+    (ptr: p + 1 int32, idx: int32), each pixel's neighbours in the order up,
+    left, right, down.  Symmetric: k in N_j exactly when j in N_k."""
+    G = int(grid)
+    ptr, idx = [0], []
+    for r in range(G):
+        for c in range(G):
+            for rr, cc in ((r - 1, c), (r, c - 1), (r, c + 1), (r + 1, c)):
+                if 0 <= rr < G and 0 <= cc < G:
+                    idx.append(rr * G + cc)
+            ptr.append(len(idx))
+    return np.asarray(ptr, dtype=np.int32), np.asarray(idx, dtype=np.int32)
+
+
+@dataclasses.dataclass
+class PetProblem:
+    """One PET reconstruction: counts y (d) along the lines of E (d x p,
+    raw geometry), the neighbourhood CSR and the penalty constants mu (one
+    image per value), started from lambda = 1 (Algorithm 2)."""
+    name: str
+    E: np.ndarray          # float32 (d, p), row-major, unscaled lengths
+    y: np.ndarray          # float32 (d,), counts
+    nbr_ptr: np.ndarray    # int32 (p + 1,)
+    nbr_idx: np.ndarray    # int32 (nnz,)
+    mu: tuple
+    iters: int
+    grid: int
+    lam_true: np.ndarray   # float64 (p,), the phantom the counts were drawn from
+
+    @property
+    def d(self):
+        return self.E.shape[0]
+
+    @property
+    def p(self):
+        return self.E.shape[1]
+
+
+def pet_problem(grid: int, ndet: int, seed: int, mean_count: float = 20.0,
+                mu=(0.0, 1e-7, 1e-6, 1e-5), iters: int = 10,
+                name: str = "pet") -> PetProblem:
+    """y_i ~ Poisson((E lam_true)_i) with the phantom scaled so the mean
+    expected count per line is `mean_count`; numpy's Generator seeded by
+    (seed, STREAM_PET_COUNTS)."""
+    E = pet_system_matrix(grid, ndet)
+    lam = pet_phantom(grid)
+    proj = E.astype(np.float64) @ lam
+    lam = lam * (mean_count / proj.mean())
+    rng = np.random.default_rng([int(seed), STREAM_PET_COUNTS])
+    y = rng.poisson(E.astype(np.float64) @ lam).astype(np.float32)
+    ptr, idx = grid_neighbours(grid)
+    return PetProblem(name, E, y, ptr, idx, tuple(float(m) for m in mu), iters, grid, lam)
+
+
+PET = dict(name="pet_64x64_d2016", grid=64, ndet=64, iters=100)
+PET_LARGE = dict(name="pet_128x128_d8128", grid=128, ndet=128, iters=20)
+
+
+def pet(seed: int = BASE_SEED + 6, iters: int = None) -> PetProblem:
+    """The paper's PET example shape: 64 x 64 pixels, 2016 lines."""
+    c = PET
+    return pet_problem(c["grid"], c["ndet"], seed, iters=iters or c["iters"], name=c["name"])
+
+
+def pet_large(seed: int = BASE_SEED + 7, iters: int = None) -> PetProblem:
+    """A larger scanner: 128 x 128 pixels, 128 detectors, 8128 lines (E is
+    532 MB, four times the L2 cache)."""
+    c = PET_LARGE
+    return pet_problem(c["grid"], c["ndet"], seed, iters=iters or c["iters"], name=c["name"])
