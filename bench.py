@@ -428,6 +428,95 @@ def time_poisson(ws, clocks, steps=3, iters=10):
             "loglik_start": L0, "loglik_end": L1}
 
 
+def pet_stored_objectives(name):
+    """The float64 oracle's objectives per penalty constant on a PET
+    workload, from tests/golden/pet_objectives.json (written by
+    tests/golden/make_pet_objectives.py from the oracle alone), or None."""
+    path = os.path.join(ROOT, "tests", "golden", "pet_objectives.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)[name]
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def time_pet(ws, steps=3):
+    """Penalised PET reconstruction (Section 3.2, Algorithm 2) through
+    pet_step, inputs resident: the paper's example shape (64 x 64 pixels,
+    2016 lines, E 33 MB: L2-resident, so launch- and latency-bound) and a
+    larger scanner (128 x 128 pixels, 8128 lines, E 532 MB: HBM-bound), each
+    with the four penalty constants reconstructed together (one pass over E
+    serves all four) and with one image alone.  One step = the workload's
+    iterations from lambda = 1.  Per iteration the two kernels each stream E
+    once: 4 d p bytes each (plus vectors of d and p), the roofline's
+    algorithmic bytes per launch."""
+    import numpy as np
+    import torch
+    from paper_1003_3272_gb300 import nmf, synth
+    pk = peaks()
+    out = {}
+    stream = torch.cuda.current_stream()
+    for build in (synth.pet, synth.pet_large):
+        pr = build()
+        E = torch.from_numpy(pr.E).cuda()
+        y = torch.from_numpy(pr.y).cuda()
+        ent = {"d": pr.d, "p": pr.p, "iters_per_step": pr.iters,
+               "E_bytes": int(pr.E.nbytes), "l2_resident": bool(pr.E.nbytes < 100e6)}
+        stored = pet_stored_objectives(pr.name)
+        for mu in (pr.mu, pr.mu[-1:]):
+            k = len(mu)
+            lam = torch.ones(k, pr.p, device="cuda")
+            with nmf.PET(E, y, pr.nbr_ptr, pr.nbr_idx, mu, lam=lam, stream=stream) as m:
+                m.step(2)                                   # warm-up
+                torch.cuda.synchronize()
+                m.profile(True)
+                barrier(ws)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                fs = None
+                e0.record(stream)
+                for _ in range(steps):
+                    m.restart()                             # Algorithm 2's start
+                    m.step(pr.iters)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = max_over_ranks(e0.elapsed_time(e1), ws)
+                fw_ms, fw_n = m.profile_read(0)
+                bk_ms, bk_n = m.profile_read(1)
+                m.profile(False)
+                fs = m.objective()
+            its = steps * pr.iters
+            bytes_l = 4.0 * pr.d * pr.p + 4.0 * k * (pr.d + pr.p)
+            fw_us = fw_ms / max(fw_n, 1) * 1e3
+            bk_us = bk_ms / max(bk_n, 1) * 1e3
+            leg = {"images": k, "mu": list(mu),
+                   "value": round(job_rate(its * k, ms / 1e3, ws), 1),
+                   "unit": "image-iterations/s",
+                   "iterations_per_s": round(job_rate(its, ms / 1e3, ws), 1),
+                   "ms_per_iteration": round(ms / its, 5),
+                   "forward_us": round(fw_us, 2), "back_us": round(bk_us, 2),
+                   "roofline": {"bound": "hbm", "unit": "GB/s", "peak": pk["hbm_gbs"],
+                                "algorithmic_bytes_per_launch": int(bytes_l),
+                                "achieved_forward": round(bytes_l / (fw_us * 1e-6) / 1e9, 1),
+                                "achieved_back": round(bytes_l / (bk_us * 1e-6) / 1e9, 1),
+                                "frac_forward": round(bytes_l / (fw_us * 1e-6) / 1e9 / pk["hbm_gbs"], 4),
+                                "frac_back": round(bytes_l / (bk_us * 1e-6) / 1e9 / pk["hbm_gbs"], 4),
+                                "frac_iteration": round(2 * bytes_l / (ms / its * 1e-3) / 1e9
+                                                        / pk["hbm_gbs"], 4),
+                                "traffic": None},
+                   "objective": [float(v) for v in fs]}
+            if stored and stored.get("iters") == pr.iters:
+                errs = []
+                for kk, mk in enumerate(mu):
+                    fo = stored["objective"][repr(float(mk))][str(pr.iters)]
+                    errs.append(float(f"{abs(fs[kk] - fo) / abs(fo):.3e}"))
+                leg["rel_objective_error_vs_fp64_oracle"] = errs
+            ent["images_%d" % k] = leg
+        out[pr.name] = ent
+        del E, y
+        torch.cuda.empty_cache()
+    return out
+
+
 def time_converge(ws, prec="fp32", tol=1e-9, max_iters=100000):
     """Section 3's protocol on the CBCL-shaped workload (faces 361 x 2429,
     r = 10): iterate until the relative objective change drops below tol
@@ -659,6 +748,7 @@ def run_gpu(args, ws, rank, local):
             out["batched"] = time_batched("bf16x3", max(2, args.steps // 2), 2, 20, ws)
             out["converge"] = time_converge(ws)
             out["poisson"] = time_poisson(ws, clocks)
+            out["pet"] = time_pet(ws)
             if not args.no_workloads:
                 out["by_workload"] = time_workloads(ws, local, clocks)
     else:

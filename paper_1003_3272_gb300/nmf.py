@@ -49,6 +49,9 @@ EXPORTS = [
     "nmf_status_str", "nmf_last_error", "nmf_version", "nmf_restart",
     "nmf_kernel_launches", "nmf_profile_enable", "nmf_profile_read", "nmf_gram_noalloc",
     "nmf_selfcheck_div", "nmf_test_expire_next_wait", "nmf_converge", "nmf_qn_run",
+    # include/pet.h: penalised PET reconstruction (Section 3.2, Algorithm 2)
+    "pet_init", "pet_step", "pet_restart", "pet_objective", "pet_run", "pet_profile_enable",
+    "pet_profile_read", "pet_destroy", "pet_last_error",
 ]
 
 _lib = None
@@ -101,6 +104,18 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "nmf_profile_enable": ([c_p, ctypes.c_int], ctypes.c_int),
         "nmf_profile_read": ([c_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "pet_init": ([i64, i64, c_p, c_p, c_p, c_p, i32, c_p, c_p, i32, c_p,
+                      ctypes.POINTER(c_p)], ctypes.c_int),
+        "pet_step": ([c_p, ctypes.c_int], ctypes.c_int),
+        "pet_restart": ([c_p], ctypes.c_int),
+        "pet_objective": ([c_p, c_p], ctypes.c_int),
+        "pet_run": ([c_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                     ctypes.POINTER(ctypes.c_int), c_p], ctypes.c_int),
+        "pet_profile_enable": ([c_p, ctypes.c_int], ctypes.c_int),
+        "pet_profile_read": ([c_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "pet_destroy": ([c_p], None),
+        "pet_last_error": ([c_p], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -339,3 +354,100 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _pet_check(status: int, ctx=None):
+    if status != OK:
+        lib = load()
+        why = lib.pet_last_error(ctx).decode()
+        raise NMFError(status, f"{lib.nmf_status_str(status).decode()}: {why}")
+
+
+class PET:
+    """Penalised PET reconstruction (Section 3.2, Algorithm 2) through
+    ``pet_*``: E (d x p) and y (d) contiguous float32 CUDA tensors (raw
+    geometry and counts), the neighbourhood system as host CSR arrays
+    (int32), one image per penalty constant in ``mu``.  ``lam`` (nimg x p
+    float32 CUDA tensor) is updated in place; when None it is allocated and
+    set to Algorithm 2's start lambda = 1."""
+
+    def __init__(self, E, y, nbr_ptr, nbr_idx, mu, lam=None, init_ones=True, stream=None):
+        import numpy as np
+        import torch
+        for name, t in (("E", E), ("y", y)):
+            if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+        d, p = E.shape
+        if y.shape != (d,):
+            raise ValueError("y must have shape (d,)")
+        mu = np.ascontiguousarray(np.atleast_1d(np.asarray(mu, dtype=np.float64)))
+        k = len(mu)
+        if lam is None:
+            lam = torch.ones(k, p, device=E.device, dtype=torch.float32)
+            init_ones = True
+        if not (lam.is_cuda and lam.dtype == torch.float32 and lam.is_contiguous()
+                and tuple(lam.shape) == (k, p)):
+            raise ValueError("lam must be a contiguous float32 CUDA tensor of shape (nimg, p)")
+        self.lib = load()
+        self.E, self.y, self.lam, self.mu = E, y, lam, mu
+        self.d, self.p, self.nimg = d, p, k
+        self._ptr = np.ascontiguousarray(nbr_ptr, dtype=np.int32)
+        self._idx = np.ascontiguousarray(nbr_idx, dtype=np.int32)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        ctx = ctypes.c_void_p()
+        _pet_check(self.lib.pet_init(
+            d, p, _ptr(E), _ptr(y), self._ptr.ctypes.data_as(ctypes.c_void_p),
+            self._idx.ctypes.data_as(ctypes.c_void_p), k, mu.ctypes.data_as(ctypes.c_void_p),
+            _ptr(lam), int(bool(init_ones)), _stream_handle(self.stream), ctypes.byref(ctx)))
+        self.ctx = ctx
+
+    def step(self, iters: int = 1):
+        _pet_check(self.lib.pet_step(self.ctx, int(iters)), self.ctx)
+
+    def restart(self):
+        """Algorithm 2's start (lambda = 1) on the same inputs."""
+        _pet_check(self.lib.pet_restart(self.ctx), self.ctx)
+
+    def objective(self):
+        import numpy as np
+        out = np.empty(self.nimg, dtype=np.float64)
+        _pet_check(self.lib.pet_objective(self.ctx, out.ctypes.data_as(ctypes.c_void_p)),
+                   self.ctx)
+        return out
+
+    def run(self, max_iters: int, tol: float = 1e-9, check_every: int = 1):
+        import numpy as np
+        done = ctypes.c_int()
+        out = np.empty(self.nimg, dtype=np.float64)
+        _pet_check(self.lib.pet_run(self.ctx, int(max_iters), float(tol), int(check_every),
+                                    ctypes.byref(done), out.ctypes.data_as(ctypes.c_void_p)),
+                   self.ctx)
+        return done.value, out
+
+    def profile(self, on: bool = True):
+        _pet_check(self.lib.pet_profile_enable(self.ctx, int(bool(on))), self.ctx)
+
+    def profile_read(self, kind: int):
+        """(total ms, launches): 0 forward projection, 1 back projection with
+        the update, 2 objective."""
+        ms, cnt = ctypes.c_double(), ctypes.c_int64()
+        _pet_check(self.lib.pet_profile_read(self.ctx, int(kind), ctypes.byref(ms),
+                                             ctypes.byref(cnt)), self.ctx)
+        return ms.value, cnt.value
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.pet_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

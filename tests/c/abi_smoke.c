@@ -1,7 +1,9 @@
 /* A C99 program that uses libnmf.so through include/nmf.h alone: seeded
  * start, ten MM iterations of a small problem in the split-BF16x3 form, the
  * objective before and after (the MM descent property, Section 3.1), the
- * error path of a bad argument, then cleanup.  Exit status 0 on success. */
+ * error path of a bad argument, then cleanup; then a tiny penalised PET
+ * reconstruction through include/pet.h (Section 3.2: the penalised
+ * loglikelihood rises).  Exit status 0 on success. */
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -9,6 +11,7 @@
 #include <cuda_runtime_api.h>
 
 #include "nmf.h"
+#include "pet.h"
 
 #define CHECK(x)                                                        \
   do {                                                                  \
@@ -54,6 +57,33 @@ int main(void) {
   cudaFree(W);
   cudaFree(H);
   free(hV);
+
+  /* PET: 4 lines through 3 pixels in a row, neighbours 0-1-2 */
+  {
+    const float hE[12] = {1.0f, 0.5f, 0.0f, 0.0f, 1.0f, 1.0f, 0.3f, 0.3f, 0.3f, 1.0f, 0.0f, 2.0f};
+    const float hy[4] = {4.0f, 7.0f, 2.0f, 0.0f};
+    const int32_t ptr[4] = {0, 1, 3, 4}, idx[4] = {1, 0, 2, 1};
+    const double mu[2] = {0.0, 0.1};
+    float *E = NULL, *y = NULL, *lam = NULL;
+    CHECK(cudaMalloc((void**)&E, sizeof hE) == cudaSuccess);
+    CHECK(cudaMalloc((void**)&y, sizeof hy) == cudaSuccess);
+    CHECK(cudaMalloc((void**)&lam, 2 * 3 * sizeof(float)) == cudaSuccess);
+    CHECK(cudaMemcpy(E, hE, sizeof hE, cudaMemcpyHostToDevice) == cudaSuccess);
+    CHECK(cudaMemcpy(y, hy, sizeof hy, cudaMemcpyHostToDevice) == cudaSuccess);
+    pet_ctx* pc = NULL;
+    CHECK(pet_init(4, 3, E, y, ptr, idx, 2, mu, lam, 1, NULL, &pc) == NMF_OK && pc != NULL);
+    double g0[2], g1[2];
+    CHECK(pet_objective(pc, g0) == NMF_OK);
+    CHECK(pet_step(pc, 20) == NMF_OK);
+    CHECK(pet_objective(pc, g1) == NMF_OK);
+    printf("pet f0 = %.9g %.9g  f20 = %.9g %.9g\n", g0[0], g0[1], g1[0], g1[1]);
+    CHECK(g1[0] > g0[0] && g1[1] > g0[1]);
+    CHECK(pet_step(NULL, 1) == NMF_EINVAL && pet_last_error(NULL)[0] != '\0');
+    pet_destroy(pc);
+    cudaFree(E);
+    cudaFree(y);
+    cudaFree(lam);
+  }
   printf("ok %s\n", nmf_version());
   return 0;
 }

@@ -25,13 +25,13 @@ def _declared():
             continue
         src = open(os.path.join(ROOT, "include", f)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        names += re.findall(r"\b(nmf_\w+)\s*\(", src)
+        names += re.findall(r"\b((?:nmf|pet)_\w+)\s*\(", src)
     return sorted(set(names))
 
 
 def test_every_declared_symbol_is_exported(lib):
     names = _declared()
-    assert "nmf_init" in names and "nmf_batched_step" in names
+    assert "nmf_init" in names and "nmf_batched_step" in names and "pet_init" in names
     for name in names:
         assert hasattr(lib, name), name
 
@@ -138,3 +138,49 @@ def test_batched_rejections_on_the_host(lib):
     assert lib.nmf_batched_init(2, cfgs, ptrs, ptrs, ptrs, None, ctypes.byref(out)) == nmf.EUNSUPPORTED
     assert lib.nmf_batched_init(0, cfgs, ptrs, ptrs, ptrs, None, ctypes.byref(out)) == nmf.EINVAL
     assert lib.nmf_batched_step(None, 1) == nmf.EINVAL
+
+
+def _pet_init(lib, d=6, p=4, nimg=1, mu=(0.0,), ptr=None, idx=None):
+    import numpy as np
+    if ptr is None:   # a chain 0-1-2-3
+        ptr = [0, 1, 3, 5, 6]
+    if idx is None:
+        idx = [1, 0, 2, 1, 3, 2]
+    ptr = np.asarray(ptr, dtype=np.int32)
+    idx = np.asarray(idx, dtype=np.int32)
+    mu = np.asarray(mu, dtype=np.float64)
+    ctx = ctypes.c_void_p(123)
+    dummy = ctypes.c_void_p(16)
+    st = lib.pet_init(d, p, dummy, dummy, ptr.ctypes.data_as(ctypes.c_void_p),
+                      idx.ctypes.data_as(ctypes.c_void_p), nimg,
+                      mu.ctypes.data_as(ctypes.c_void_p), dummy, 1, None, ctypes.byref(ctx))
+    return st, ctx
+
+
+@pytest.mark.parametrize("bad", [
+    dict(d=0), dict(p=0), dict(nimg=0, mu=()), dict(nimg=9, mu=(0.0,) * 9),
+    dict(mu=(-1.0,)), dict(mu=(float("nan"),)), dict(mu=(float("inf"),)),
+    dict(ptr=[1, 1, 3, 5, 6]),                               # does not start at 0
+    dict(ptr=[0, 2, 1, 5, 6]),                               # decreasing
+    dict(ptr=[0, 1, 3, 5, 6], idx=[1, 0, 2, 1, 3, 4]),       # out of range
+    dict(ptr=[0, 1, 3, 5, 6], idx=[1, 1, 2, 1, 3, 2]),       # pixel 1 its own neighbour
+    dict(ptr=[0, 1, 2, 4, 5], idx=[1, 2, 1, 3, 2]),          # 0 -> 1 without 1 -> 0
+])
+def test_pet_init_rejects_bad_arguments_on_the_host(lib, bad):
+    from paper_1003_3272_gb300 import nmf
+    st, ctx = _pet_init(lib, **bad)
+    assert st == nmf.EINVAL
+    assert ctx.value is None
+    assert len(lib.pet_last_error(None)) > 0
+
+
+def test_pet_null_arguments(lib):
+    from paper_1003_3272_gb300 import nmf
+    ctx = ctypes.c_void_p()
+    assert lib.pet_init(4, 4, None, None, None, None, 1, None, None, 1, None,
+                        ctypes.byref(ctx)) == nmf.EINVAL
+    assert lib.pet_step(None, 1) == nmf.EINVAL
+    assert lib.pet_objective(None, None) == nmf.EINVAL
+    done = ctypes.c_int()
+    assert lib.pet_run(None, 10, 1e-9, 1, ctypes.byref(done), None) == nmf.EINVAL
+    lib.pet_destroy(None)  # no-op
