@@ -332,17 +332,65 @@ def roofline(prec, p, n, r, res, clocks, workload="planted_8192x8192_r50"):
     return roof
 
 
-def time_batched(prec, steps, warmup, iters, ws):
+def batched_stored_objectives():
+    """The float64 oracle's objectives after 100 iterations of sampled
+    instances of the batched workload, from tests/golden/batched_objectives.json
+    (written by tests/golden/make_batched_objectives.py from the oracle
+    alone), or None."""
+    path = os.path.join(ROOT, "tests", "golden", "batched_objectives.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return None
+
+
+def time_singles(probs, prec, iters, Vs):
+    """The same instances one at a time, each through its own context and
+    nmf_step (two launches per iteration each): the comparison for the
+    grouped launch.  Returns instance-iterations/s."""
+    import torch
+    from paper_1003_3272_gb300 import nmf
+    stream = torch.cuda.current_stream()
+    ctxs, facs = [], []
+    for pr, V in zip(probs, Vs):
+        W = torch.from_numpy(pr.W0).cuda()
+        H = torch.from_numpy(pr.H0).cuda()
+        facs.append((W, H))
+        ctxs.append(nmf.NMF(V, W, H, eps=pr.eps, prec=prec, stream=stream))
+    for m in ctxs:
+        m.step(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for m in ctxs:
+        m.step(iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    for m in ctxs:
+        m.close()
+    del facs
+    torch.cuda.empty_cache()
+    return len(probs) * iters / (ms / 1e3)
+
+
+def time_batched(prec, steps, warmup, iters, ws, singles=True):
     """The batched workload: 512 independent problems (p, n in 64..2048, r in
     4..32), `iters` MM iterations per step through nmf_batched_step (one
-    grouped persistent launch per half step, CUDA graph)."""
+    grouped persistent launch per half step, CUDA graph; the timing does not
+    depend on the values).  Beside it the same instances one by one through nmf_step
+    in plain FP32 and in the same precision, and the objective error after
+    100 iterations against the stored oracle values of sampled instances."""
     import numpy as np
     import torch
     from paper_1003_3272_gb300 import nmf, synth
     probs = synth.batch(iters=iters)
     Vs = [torch.from_numpy(pr.V).cuda() for pr in probs]
-    Ws = [torch.from_numpy(pr.W0).cuda() for pr in probs]
-    Hs = [torch.from_numpy(pr.H0).cuda() for pr in probs]
+    W0 = [torch.from_numpy(pr.W0).cuda() for pr in probs]
+    H0 = [torch.from_numpy(pr.H0).cuda() for pr in probs]
+    Ws = [w.clone() for w in W0]
+    Hs = [h.clone() for h in H0]
     b = nmf.Batch(Vs, Ws, Hs, prec=prec)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
@@ -358,22 +406,49 @@ def time_batched(prec, steps, warmup, iters, ws):
     torch.cuda.synchronize()
     launches = nmf.kernel_launches() - l0
     ms = max_over_ranks(e0.elapsed_time(e1), ws)
-    f = b.objective()
+    schedule = b.schedule
+    b.close()
+    # accuracy: 100 iterations from the seeded start, sampled instances
+    acc = None
+    stored = batched_stored_objectives()
+    if stored:
+        for w, w0 in zip(Ws, W0):
+            w.copy_(w0)
+        for h, h0 in zip(Hs, H0):
+            h.copy_(h0)
+        b2 = nmf.Batch(Vs, Ws, Hs, prec=prec)
+        b2.step(stored["iters"])
+        f = b2.objective()
+        b2.close()
+        errs = {k: abs(f[int(k)] - v) / v for k, v in stored["objective"].items()}
+        acc = {"iterations": stored["iters"], "instances": sorted(int(k) for k in errs),
+               "max": float(f"{max(errs.values()):.3e}"),
+               "median": float(f"{np.median(list(errs.values())):.3e}"),
+               "source": "tests/golden/batched_objectives.json (float64 oracle, "
+                         "tests/golden/make_batched_objectives.py)"}
     vb = {"fp32": 4, "tf32": 4, "bf16x3": 4, "bf16": 2}[prec]
     bytes_it = sum(2 * pr.p * pr.n * vb for pr in probs)
     per_it_s = ms / 1e3 / (steps * iters)
+    value = len(probs) * iters * steps * ws / (ms / 1e3)
     out = {"metric": "instance MM iterations/s", "precision": prec, "instances": len(probs),
            "iters_per_step": iters, "steps": steps, "ms_per_step": round(ms / steps, 3),
-           "value": round(len(probs) * iters * steps * ws / (ms / 1e3), 1),
-           "unit": "instance-iterations/s",
+           "value": round(value, 1), "unit": "instance-iterations/s",
            "aggregate_gbs": round(bytes_it / per_it_s / 1e9, 1),
            "hbm_frac": round(bytes_it / per_it_s / 1e9 / peaks()["hbm_gbs"], 4),
            "V_bytes_per_iteration": int(bytes_it), "gpu_launches": int(launches),
-           "mean_objective": float(np.mean(f)),
+           "schedule": schedule, "rel_objective_error_vs_fp64_oracle": acc,
            "config": "synth.batch(): 512 instances, p,n ~ U{64..2048}, r ~ U{4..32}, "
                      "V ~ U[0,1), seeded"}
-    b.close()
-    del Vs, Ws, Hs
+    if singles:
+        sing = {}
+        for sp in ("fp32", prec):
+            rate = time_singles(probs, sp, max(2, iters // 10), Vs)
+            sing[sp] = {"value": round(rate, 1), "unit": "instance-iterations/s",
+                        "api": f"one context per instance, nmf_step, {sp}"}
+        out["one_by_one"] = sing
+        out["speedup_vs_fp32"] = round(value / sing["fp32"]["value"], 2)
+        out["speedup_vs_one_by_one_same_precision"] = round(value / sing[prec]["value"], 2)
+    del Vs, Ws, Hs, W0, H0
     torch.cuda.empty_cache()
     return out
 
@@ -643,7 +718,7 @@ def run_batched_line(args, ws, local):
     sampler = ClockSampler(local)
     sampler.start()
     w0 = time.perf_counter()
-    b = time_batched(args.prec, args.steps, args.warmup, 100, ws)
+    b = time_batched(args.prec, args.steps, args.warmup, 100, ws, singles=not args.no_extras)
     clocks = sampler.stop((w0, time.perf_counter()))
     pk = peaks()
     return {
@@ -660,7 +735,9 @@ def run_batched_line(args, ws, local):
                      "unit": "GB/s", "frac": b["hbm_frac"], "traffic": None,
                      "kernel": "k_batched_tc (whole graph-captured iteration)"},
         "e2e": None, "gpu_launches": b["gpu_launches"], "clocks": clocks,
-        "objective_mean": b["mean_objective"],
+        "schedule": b["schedule"],
+        "accuracy": b["rel_objective_error_vs_fp64_oracle"],
+        "one_by_one": b.get("one_by_one"), "speedup_vs_fp32": b.get("speedup_vs_fp32"),
     }
 
 
@@ -745,7 +822,7 @@ def run_gpu(args, ws, rank, local):
         out["by_precision"] = by
         out["accuracy"] = accuracy(wname, iters, objs)
         if args.workload == "planted":
-            out["batched"] = time_batched("bf16x3", max(2, args.steps // 2), 2, 20, ws)
+            out["batched"] = time_batched("bf16x3", 2, 2, 100, ws)
             out["converge"] = time_converge(ws)
             out["poisson"] = time_poisson(ws, clocks)
             out["pet"] = time_pet(ws)

@@ -215,8 +215,25 @@ nmf_status nmf_batched_init(int count, const nmf_config* cfgs,
                             const float* const* V, float* const* W,
                             float* const* H, void* stream, nmf_batch** out);
 nmf_status nmf_batched_step(nmf_batch* b, int iters);
-/* f_out: host array of `count` doubles.  Synchronises.                    */
+/* f_out: host array of `count` doubles.  Synchronises.  NMF_ETIMEOUT if a
+ * bounded device wait of an earlier step ran out (the error is then
+ * cleared).                                                                */
 nmf_status nmf_batched_objective(nmf_batch* b, double* f_out);
+/* The schedule the autotuner chose at nmf_batched_init ("policy/grid":
+ * lpt, glpt or rr over `grid` persistent blocks).  No counterpart in the
+ * paper.  The environment variable NMF_BATCHED_SCHEDULE, read at init,
+ * forces one candidate by that name (NMF_EINVAL if it names none), and
+ * NMF_TUNE_CACHE (a file path) caches the choice per batch signature.
+ * Never NULL; "" for b == NULL.                                            */
+const char* nmf_batched_schedule(const nmf_batch* b);
+/* Failure-detection test hook (no counterpart in the paper): the next
+ * nmf_batched_step iteration is launched outside its graph with every
+ * block's first pipeline stage armed for 16 bytes more than its copies
+ * bring, so that every bounded wait on it runs out (about 3 s per half
+ * step) without a fault: the blocks stop before updating any factor, the
+ * next nmf_batched_objective reports NMF_ETIMEOUT, and later steps run
+ * normally.  NMF_EINVAL for b == NULL.                                      */
+nmf_status nmf_batched_test_expire_next_wait(nmf_batch* b);
 void nmf_batched_destroy(nmf_batch* b);
 
 /* ---- Gram matrix without allocation --------------------------------------

@@ -70,6 +70,7 @@ struct BatchParams {
   int half;
   int* err;
   double* gitem;              // [slot][kBR * kBR] Grams of the items' new rows
+  uint32_t test_extra_tx;     // test hook: extra bytes armed on each block's first stage
 };
 
 template <int PREC>
@@ -188,7 +189,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(const BatchParams a)
           break;
         }
         const uint32_t fb = ptx::smem_u32(&full_bar[s]);
-        ptx::mbar_expect_tx(fb, bytes);
+        // (test hook: the first stage armed for more bytes than are copied, so
+        // its barrier never completes and every wait on it runs out)
+        ptx::mbar_expect_tx(fb, bytes + (g == 0 ? a.test_extra_tx : 0u));
         const int32_t xb = (int32_t)((int64_t)it.y * nkb + kb);
         ptx::tma_load_3d(x_addr(s, 0), mp + 0, 0, 0, xb, fb);
         if (X3) ptx::tma_load_3d(x_addr(s, 1), mp + 1, 0, 0, xb, fb);
@@ -679,6 +682,8 @@ struct nmf_batch {
   cudaGraphExec_t graph = nullptr;
   std::string schedule = "lpt";
   std::string err;
+  bool test_expire = false;        // nmf_batched_test_expire_next_wait
+  uint32_t test_extra_tx = 0;      // passed to the grouped kernel
 };
 
 namespace {
@@ -699,7 +704,11 @@ cudaError_t balloc(nmf_batch* b, void** p, size_t bytes) {
 
 // Work schedule of one half step: items (instance, tile) distributed over
 // `grid` blocks.  "lpt": longest items first onto the least-loaded block;
-// "rr": items in instance order, round robin.  Cost of an item = k-blocks.
+// "glpt": the same with each instance's tiles kept together (instances by
+// decreasing item cost, their tiles in order), so that the tiles of one
+// instance land on different blocks at about the same time and share the
+// instance's factor plane in L2; "rr": items in instance order, round robin.
+// Cost of an item = k-blocks.
 void make_schedule(const std::vector<std::pair<int, int>>& items, const std::vector<int>& cost,
                    int grid, const std::string& policy, std::vector<int2>& out,
                    std::vector<int>& off) {
@@ -709,7 +718,12 @@ void make_schedule(const std::vector<std::pair<int, int>>& items, const std::vec
   } else {
     std::vector<int> order(items.size());
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    if (policy == "glpt")   // items of an instance are contiguous and equally costly
+      std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return cost[x] != cost[y] ? cost[x] > cost[y] : items[x].first < items[y].first;
+      });
+    else
+      std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
     std::vector<long long> load(grid, 0);
     for (int i : order) {
       int best = 0;
@@ -739,7 +753,7 @@ cudaError_t launch_batched_tc(nmf_batch* b, int half) {
     done = true;
   }
   BatchParams prm{b->d_inst, b->d_maps, b->d_items[half], b->d_off[half], half, b->d_err,
-                  b->d_gitem};
+                  b->d_gitem, b->test_extra_tx};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)b->grid[half]);
   cfg.blockDim = dim3(kThreads);
@@ -994,8 +1008,8 @@ nmf_status nmf_batched_init(int count, const nmf_config* cfgs, const float* cons
   // a warm-up) and the fastest kept.  NMF_TUNE_CACHE (a file path) caches the
   // choice per batch signature.
   std::vector<std::pair<std::string, int>> cands;
-  for (const char* pol : {"lpt", "rr"})
-    for (int g : {b->sms, b->sms - b->sms / 8}) cands.push_back({pol, g});
+  for (const char* pol : {"lpt", "glpt", "rr"})
+    for (int g : {b->sms, b->sms - b->sms / 8, b->sms - b->sms / 4}) cands.push_back({pol, g});
   std::string sig;
   {
     std::ostringstream os;
@@ -1011,7 +1025,18 @@ nmf_status nmf_batched_init(int count, const nmf_config* cfgs, const float* cons
   }
   const char* cache = std::getenv("NMF_TUNE_CACHE");
   int chosen = -1;
-  if (cache) {
+  // NMF_BATCHED_SCHEDULE="policy/grid" forces one candidate (tests check
+  // each against the oracle); an unknown value is an error.
+  if (const char* force = std::getenv("NMF_BATCHED_SCHEDULE")) {
+    for (size_t c = 0; c < cands.size(); ++c)
+      if (cands[c].first + "/" + std::to_string(cands[c].second) == force) chosen = (int)c;
+    if (chosen < 0) {
+      nmf_batched_destroy(b);
+      return bfail(nullptr, NMF_EINVAL,
+                   std::string("NMF_BATCHED_SCHEDULE names no candidate: ") + force);
+    }
+  }
+  if (cache && chosen < 0) {
     std::ifstream in(cache);
     std::string k, pol;
     int g;
@@ -1083,7 +1108,7 @@ nmf_status nmf_batched_init(int count, const nmf_config* cfgs, const float* cons
       count_launches(2);
     }
     if ((e = start_gram(b)) != cudaSuccess) return fail_cuda(e, "gram");
-    if (cache) {
+    if (cache && !std::getenv("NMF_BATCHED_SCHEDULE")) {
       std::ofstream o(cache, std::ios::app);
       o << sig << " " << cands[chosen].first << " " << cands[chosen].second << "\n";
     }
@@ -1114,6 +1139,16 @@ nmf_status nmf_batched_init(int count, const nmf_config* cfgs, const float* cons
 
 nmf_status nmf_batched_step(nmf_batch* b, int iters) {
   if (!b || iters < 0) return bfail(b, NMF_EINVAL, "bad arguments to nmf_batched_step");
+  if (b->test_expire && iters > 0) {
+    // both half steps of this iteration, launched directly (not from the
+    // graph) with every block's first stage armed for 16 bytes it never gets
+    b->test_expire = false;
+    b->test_extra_tx = 16;
+    cudaError_t e = run_iteration(b);
+    b->test_extra_tx = 0;
+    if (e != cudaSuccess) return bfail(b, NMF_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+    --iters;
+  }
   for (int it = 0; it < iters; ++it) {
     cudaError_t e = cudaGraphLaunch(b->graph, b->st);
     if (e != cudaSuccess) return bfail(b, NMF_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
@@ -1141,6 +1176,16 @@ nmf_status nmf_batched_objective(nmf_batch* b, double* f_out) {
     return bfail(b, NMF_ETIMEOUT, "a bounded device wait expired; results are invalid");
   }
   std::memcpy(f_out, b->h_f, sizeof(double) * b->count);
+  return NMF_OK;
+}
+
+const char* nmf_batched_schedule(const nmf_batch* b) {
+  return b ? b->schedule.c_str() : "";
+}
+
+nmf_status nmf_batched_test_expire_next_wait(nmf_batch* b) {
+  if (!b) return bfail(nullptr, NMF_EINVAL, "batch is NULL");
+  b->test_expire = true;
   return NMF_OK;
 }
 

@@ -10,13 +10,16 @@
 // shared memory and the helper warps (tc_epi.cuh), which formed the other
 // factor's Gram and the denominators during the stream, finish the update.
 // The difference: the product is accumulated with float32 FMAs on the SM
-// cores by eight compute warps (thread tile 4 rows x TR ranks, RPAD = 8 TR;
-// for TR <= 4, 8 rows in two groups that split each stage's K, their partial
-// tiles added in a fixed order), reading the swizzled stages with
+// cores by eight compute warps (thread tile 8 rows x TR ranks, TR <= 8; the
+// warps form NKG groups that split each stage's K, their partial tiles added
+// in a fixed order, see F32Shape), reading the swizzled stages with
 // bank-conflict-free 16-byte loads.
 //
-// Warps: 0 = TMA producer (one lane); 1-8 = compute; 9-11 = helpers.
+// Warps: 0 = TMA producer (one lane); 1-3 = helpers; 4-11 = compute (two
+// warpgroups, which take registers from warpgroup 0 by setmaxnreg).
 #include <cooperative_groups.h>
+
+#include <type_traits>
 
 #include "epilogue.cuh"
 #include "tc.cuh"
@@ -29,9 +32,16 @@ namespace nmf {
 namespace {
 
 constexpr int kThreads = 384;
-constexpr int kCompute0 = 32;      // first compute thread
-constexpr int kHelper0 = 288;      // first helper thread
-constexpr int kNH = 96;            // helper threads (warps 9-11)
+constexpr int kHelper0 = 32;       // first helper thread (warps 1-3)
+constexpr int kNH = 96;            // helper threads
+constexpr int kCompute0 = 128;     // first compute thread (warps 4-11)
+// registers a thread after the split (setmaxnreg); the kernel is built with
+// kRegsLaunch (= 65536 / 384, rounded down to a multiple of 8)
+constexpr int kRegsLaunch = 168;
+constexpr int kRegsWG0 = 136;
+constexpr int kRegsCompute = 184;
+static_assert(128 * kRegsWG0 + 256 * kRegsCompute == kThreads * kRegsLaunch,
+              "the register split must add up to the launch's registers");
 constexpr int kBM = 128;
 constexpr int kKB = 32;            // float32 values of K per stage (128 bytes)
 constexpr uint64_t kWaitLimitNs = 1500ull * 1000 * 1000;
@@ -58,9 +68,23 @@ struct F32Params {
   int* err;
 };
 
+// Compute-thread tile: every compute thread accumulates 8 rows x TR ranks;
+// the 8 warps form NKG groups that split each stage's K (group g takes the
+// stage's 16-byte K chunks [g 8 / NKG, (g + 1) 8 / NKG)), so TR = RPAD NKG /
+// 16.  NKG is chosen so that TR is close to 8: each value a thread reads
+// from shared memory then feeds TR (X) or 8 (Y) FMAs, which keeps the FMA
+// pipe ahead of the shared-memory bandwidth (one 128-byte wavefront per
+// clock, four per 16-byte load).
+template <int RPAD>
+__host__ __device__ constexpr int f32_groups() {
+  return RPAD <= 16 ? 8 : RPAD <= 32 ? 4 : RPAD <= 64 ? 2 : 1;
+}
+
 template <int RPAD>
 struct F32Shape {
-  static constexpr int TR = RPAD / 8;
+  static constexpr int NKG = f32_groups<RPAD>();
+  static constexpr int TR = RPAD * NKG / 16;
+  static_assert(TR * 16 == RPAD * NKG && TR >= 1 && TR <= 8, "rank padding of the FP32 tile");
   static constexpr int X_BYTES = kBM * 128;
   static constexpr int Y_BYTES = RPAD * 128;
   static constexpr int STAGE = X_BYTES + Y_BYTES;
@@ -73,7 +97,8 @@ struct F32Shape {
   static constexpr int STAGES_RAW = (kSmemMax - DED - 2048) / STAGE;
   static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
   static constexpr int RING = STAGES * STAGE;
-  static constexpr int MAIN = RING > ACC + NSB ? RING : ACC + NSB;
+  // after the stream: the K groups' partial tiles, then the cluster sums Ns
+  static constexpr int MAIN = RING > NKG * ACC + NSB ? RING : NKG * ACC + NSB;
   static constexpr int SMEM = MAIN + DED + 1024;
   static_assert(STAGES >= 2, "pipeline needs two stages");
   static_assert(Y_BYTES % 1024 == 0, "stage slots stay 1024-byte aligned");
@@ -129,8 +154,7 @@ k_stream_f32(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUt
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = ptx::smem_u32(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool compute = threadIdx.x >= kCompute0 && threadIdx.x < kHelper0;
-  const bool helper = threadIdx.x >= kHelper0;
+  const bool helper = threadIdx.x >= kHelper0 && threadIdx.x < kCompute0;
   const int h = threadIdx.x - kHelper0;
 
   float* Qs = reinterpret_cast<float*>(smem + Sh::MAIN);
@@ -194,169 +218,209 @@ k_stream_f32(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUt
     tcepi::helper_sync<kNH>();
   }
 
-  // compute thread layout: RT rows x TR ranks per thread.  RT = 8 (TR <= 4):
-  // two groups of four warps split each stage's K (16-byte chunks 0-3 and
-  // 4-7), rows rg + 16 i; RT = 4: one group, rows rg + 32 i.  Ranks cgi + 8 t.
-  // (The 8-row tile halves the X loads per FMA; above TR = 4 its registers
-  // cost more than that saves.)
-  constexpr int RT = TR <= 4 ? 8 : 4;
-  constexpr int NKG = RT / 4;                 // K groups
-  constexpr int TPG = 256 / NKG;              // threads per group
-  constexpr int RS = 128 / RT;                // row stride
+  // compute thread layout (see F32Shape): thread (group kgrp, row group rg,
+  // rank group cgi) accumulates rows rg + 16 i (i < 8) and ranks cgi + GR t
+  // (t < TR), GR = 16 / NKG rank groups.  Within each quarter warp the eight
+  // lanes read one X row (a broadcast) or consecutive rows, and distinct
+  // ranks, so the swizzled 16-byte loads are free of bank conflicts.
+  constexpr int NKG = Sh::NKG;
+  constexpr int GR = 16 / NKG;                // rank groups
+  constexpr int TPG = 256 / NKG;              // threads per K group
   constexpr int CPG = 8 / NKG;                // 16-byte K chunks per group and stage
   const int c = threadIdx.x - kCompute0;
-  const int kgrp = NKG == 2 ? ((c >> 7) & 1) : 0;
-  const int rg = (((c % TPG) >> 5) << 2) + (c & 3);   // 0 .. RS-1
-  const int cgi = (c & 31) >> 2;                      // 0..7
+  const int kgrp = c / TPG;
+  const int wg = (c % TPG) >> 5;
+  int rg, cgi;
+  if (GR >= 8) {
+    cgi = (lane & 7) + 8 * (wg % (GR >= 8 ? GR / 8 : 1));
+    rg = (lane >> 3) + 4 * (wg / (GR >= 8 ? GR / 8 : 1));
+  } else {
+    cgi = lane % GR;
+    rg = lane / GR + (32 / GR) * wg;
+  }
 
-  int it = 0;
-  int kb_base = 0;
-  for (int tile = cid; tile < a.tiles; tile += a.nclusters, ++it) {
-    const int64_t m0 = (int64_t)tile * kBM;
-    const int64_t row0 = m0 + (int64_t)q * R;
-    const int rows = (int)max((int64_t)0, min((int64_t)R, a.M - row0));
-    const int nkb_run = *(volatile int*)&s_abort ? 0 : nkb;
-    float acc[RT][TR];
+  // Register split (setmaxnreg): warpgroup 0 (the producer warp and the
+  // helpers) runs with kRegsWG0 registers a thread, the two compute
+  // warpgroups with kRegsCompute; the launch's 384 x 168 registers cover
+  // exactly 128 x kRegsWG0 + 256 x kRegsCompute (the host launches only
+  // when the kernel was built with 168).  Each side then runs its own copy
+  // of the tile loop, so each copy is compiled within its own budget.
+  auto tiles_loop = [&](auto role) {
+    constexpr bool kComp = decltype(role)::value;
+    int it = 0;
+    int kb_base = 0;
+    for (int tile = cid; tile < a.tiles; tile += a.nclusters, ++it) {
+      const int64_t m0 = (int64_t)tile * kBM;
+      const int64_t row0 = m0 + (int64_t)q * R;
+      const int rows = (int)max((int64_t)0, min((int64_t)R, a.M - row0));
+      const int nkb_run = *(volatile int*)&s_abort ? 0 : nkb;
+      float acc[kComp ? 8 : 1][kComp ? TR : 1];
+      if constexpr (kComp) {
+        // ---------------- float32 FMA mainloop ----------------
 #pragma unroll
-    for (int i = 0; i < RT; ++i)
+        for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int t = 0; t < TR; ++t) acc[i][t] = 0.f;
-
-    if (warp == 0 && lane == 0) {
-      // ---------------- TMA producer ----------------
-      int issued = 0, pre = 0;
-      if (it == 0) {
-        pre = nkb_run < STAGES ? nkb_run : STAGES;
-        for (int kb = 0; kb < pre; ++kb) {
-          const uint32_t fb = ptx::smem_u32(&full_bar[kb]);
-          ptx::mbar_expect_tx(fb, Sh::STAGE);
-          ptx::tma_load_3d(sbase + kb * Sh::STAGE, &tx, 0, 0,
-                           (int32_t)((int64_t)tile * a.nkbt + kbeg / kKB + kb), fb);
-        }
-        ptx::pdl_wait();
-        ptx::pdl_launch_dependents();
-        for (int kb = 0; kb < pre; ++kb)
-          ptx::tma_load_2d(sbase + kb * Sh::STAGE + Sh::X_BYTES, &ty,
-                           (int32_t)(kbeg + (int64_t)kb * kKB), 0,
-                           ptx::smem_u32(&full_bar[kb]));
-        issued = pre;
-      }
-      for (int kb = pre; kb < nkb_run; ++kb) {
-        const int g = kb_base + kb;
-        const int s = g % STAGES;
-        const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
-        if (!ptx::mbar_wait(ptx::smem_u32(&empty_bar[s]), ph ^ 1u, kWaitLimitCycles)) {
-          atomicExch(&s_abort, 1);
-          break;
-        }
-        if (*(volatile int*)&s_abort) break;
-        const uint32_t fb = ptx::smem_u32(&full_bar[s]);
-        ptx::mbar_expect_tx(fb, Sh::STAGE);
-        ptx::tma_load_3d(sbase + s * Sh::STAGE, &tx, 0, 0,
-                         (int32_t)((int64_t)tile * a.nkbt + kbeg / kKB + kb), fb);
-        ptx::tma_load_2d(sbase + s * Sh::STAGE + Sh::X_BYTES, &ty,
-                         (int32_t)(kbeg + (int64_t)kb * kKB), 0, fb);
-        issued = kb + 1;
-      }
-      for (int kb = issued - 1; kb >= 0 && kb >= issued - STAGES; --kb) {
-        const int g = kb_base + kb;
-        if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[g % STAGES]), (uint32_t)(g / STAGES) & 1u,
-                            kWaitLimitCycles))
-          atomicExch(&s_abort, 1);
-      }
-    } else if (compute) {
-      // ---------------- float32 FMA mainloop ----------------
-      for (int kb = 0; kb < nkb_run; ++kb) {
-        const int g = kb_base + kb;
-        const int s = g % STAGES;
-        const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
-        if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[s]), ph, kWaitLimitCycles)) {
-          atomicExch(&s_abort, 1);
-          break;
-        }
-        // 128-byte swizzle: 16-byte chunk c4 of row m sits at chunk c4 ^ (m & 7);
-        // every row this thread reads has the same (m & 7), so one XOR per
-        // chunk places all its loads (immediate row offsets).
-        const uint8_t* xb = smem + s * Sh::STAGE + rg * 128;
-        const uint8_t* yb = smem + s * Sh::STAGE + Sh::X_BYTES + cgi * 128;
+          for (int t = 0; t < TR; ++t) acc[i][t] = 0.f;
+        for (int kb = 0; kb < nkb_run; ++kb) {
+          const int g = kb_base + kb;
+          const int s = g % STAGES;
+          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[s]), ph, kWaitLimitCycles)) {
+            atomicExch(&s_abort, 1);
+            break;
+          }
+          // 128-byte swizzle: 16-byte chunk c4 of row m sits at chunk c4 ^ (m & 7);
+          // the rows this thread reads share (m & 7), its ranks cgi + GR t too
+          // when GR >= 8 (else the XOR is taken per rank).
+          const uint8_t* xb = smem + s * Sh::STAGE + rg * 128;
+          const uint8_t* yb = smem + s * Sh::STAGE + Sh::X_BYTES;
+#pragma unroll 1
+          for (int cc = 0; cc < CPG; ++cc) {
+            const int c4 = kgrp * CPG + cc;
+            const int xo = (c4 ^ (rg & 7)) << 4;
+            float4 xv[8], yv[TR];
 #pragma unroll
-        for (int cc = 0; cc < CPG; ++cc) {
-          const int c4 = kgrp * CPG + cc;
-          const int xo = (c4 ^ (rg & 7)) << 4;
-          const int yo = (c4 ^ cgi) << 4;
-          float4 xv[RT], yv[TR];
-#pragma unroll
-          for (int i = 0; i < RT; ++i)
-            xv[i] = *reinterpret_cast<const float4*>(xb + i * (RS * 128) + xo);
-#pragma unroll
-          for (int t = 0; t < TR; ++t)
-            yv[t] = *reinterpret_cast<const float4*>(yb + t * (8 * 128) + yo);
-#pragma unroll
-          for (int i = 0; i < RT; ++i)
+            for (int i = 0; i < 8; ++i)
+              xv[i] = *reinterpret_cast<const float4*>(xb + i * (16 * 128) + xo);
 #pragma unroll
             for (int t = 0; t < TR; ++t) {
-              acc[i][t] = fmaf(xv[i].x, yv[t].x, acc[i][t]);
-              acc[i][t] = fmaf(xv[i].y, yv[t].y, acc[i][t]);
-              acc[i][t] = fmaf(xv[i].z, yv[t].z, acc[i][t]);
-              acc[i][t] = fmaf(xv[i].w, yv[t].w, acc[i][t]);
+              const int rk = cgi + GR * t;
+              yv[t] = *reinterpret_cast<const float4*>(yb + rk * 128 + ((c4 ^ (rk & 7)) << 4));
             }
-        }
-        __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&empty_bar[s]));
-      }
-    } else if (helper && !*(volatile int*)&s_abort) {
-      if (it > 0) tcepi::load_old<RPAD, kNH>(Os, a.ep, R, row0, rows, h);
-      tcepi::compute_den_smem<RPAD, kNH>(Qs, Os, Ds, a.Gpad, a.r, R, h);
-    }
-    __syncwarp();
-    kb_base += nkb_run;
-    if (it == 0) ptx::pdl_wait();
-    __syncthreads();   // every stage consumed and landed; the ring is free
-    const bool abort = *(volatile int*)&s_abort != 0;
-
-    float* Acc = reinterpret_cast<float*>(smem);
-    float* Ns = reinterpret_cast<float*>(smem + Sh::ACC);
-    // the K groups' partial sums: group 1 stores, group 0 adds (fixed order)
-    if (compute && !abort && kgrp == NKG - 1) {
+            // one K value at a time over the whole tile: consecutive FMAs
+            // update different accumulators (no dependent chains); each
+            // accumulator still adds its K values in increasing order
 #pragma unroll
-      for (int i = 0; i < RT; ++i)
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int t = 0; t < TR; ++t) Acc[(rg + RS * i) * LDA + cgi + 8 * t] = acc[i][t];
-    }
-    if (NKG == 2) {
-      if (compute) asm volatile("bar.sync 2, 256;" ::: "memory");   // the compute warps
-      if (compute && !abort && kgrp == 0) {
+              for (int t = 0; t < TR; ++t) acc[i][t] = fmaf(xv[i].x, yv[t].x, acc[i][t]);
 #pragma unroll
-        for (int i = 0; i < RT; ++i)
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
-          for (int t = 0; t < TR; ++t) {
-            float* p = &Acc[(rg + RS * i) * LDA + cgi + 8 * t];
-            *p = acc[i][t] + *p;
+              for (int t = 0; t < TR; ++t) acc[i][t] = fmaf(xv[i].y, yv[t].y, acc[i][t]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+              for (int t = 0; t < TR; ++t) acc[i][t] = fmaf(xv[i].z, yv[t].z, acc[i][t]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+              for (int t = 0; t < TR; ++t) acc[i][t] = fmaf(xv[i].w, yv[t].w, acc[i][t]);
           }
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&empty_bar[s]));
+        }
+      } else if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        int issued = 0, pre = 0;
+        if (it == 0) {
+          pre = nkb_run < STAGES ? nkb_run : STAGES;
+          for (int kb = 0; kb < pre; ++kb) {
+            const uint32_t fb = ptx::smem_u32(&full_bar[kb]);
+            ptx::mbar_expect_tx(fb, Sh::STAGE);
+            ptx::tma_load_3d(sbase + kb * Sh::STAGE, &tx, 0, 0,
+                             (int32_t)((int64_t)tile * a.nkbt + kbeg / kKB + kb), fb);
+          }
+          ptx::pdl_wait();
+          ptx::pdl_launch_dependents();
+          for (int kb = 0; kb < pre; ++kb)
+            ptx::tma_load_2d(sbase + kb * Sh::STAGE + Sh::X_BYTES, &ty,
+                             (int32_t)(kbeg + (int64_t)kb * kKB), 0,
+                             ptx::smem_u32(&full_bar[kb]));
+          issued = pre;
+        }
+        for (int kb = pre; kb < nkb_run; ++kb) {
+          const int g = kb_base + kb;
+          const int s = g % STAGES;
+          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          if (!ptx::mbar_wait(ptx::smem_u32(&empty_bar[s]), ph ^ 1u, kWaitLimitCycles)) {
+            atomicExch(&s_abort, 1);
+            break;
+          }
+          if (*(volatile int*)&s_abort) break;
+          const uint32_t fb = ptx::smem_u32(&full_bar[s]);
+          ptx::mbar_expect_tx(fb, Sh::STAGE);
+          ptx::tma_load_3d(sbase + s * Sh::STAGE, &tx, 0, 0,
+                           (int32_t)((int64_t)tile * a.nkbt + kbeg / kKB + kb), fb);
+          ptx::tma_load_2d(sbase + s * Sh::STAGE + Sh::X_BYTES, &ty,
+                           (int32_t)(kbeg + (int64_t)kb * kKB), 0, fb);
+          issued = kb + 1;
+        }
+        for (int kb = issued - 1; kb >= 0 && kb >= issued - STAGES; --kb) {
+          const int g = kb_base + kb;
+          if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[g % STAGES]),
+                              (uint32_t)(g / STAGES) & 1u, kWaitLimitCycles))
+            atomicExch(&s_abort, 1);
+        }
+      } else if (helper && !*(volatile int*)&s_abort) {
+        if (it > 0) tcepi::load_old<RPAD, kNH>(Os, a.ep, R, row0, rows, h);
+        tcepi::compute_den_smem<RPAD, kNH>(Qs, Os, Ds, a.Gpad, a.r, R, h);
       }
-    }
-    cluster.sync();   // every block's partial tile is in its shared memory
-    if (!abort) {
-      // rows [q R, (q+1) R) of the tile: the S partial tiles summed in rank order
-      for (int i = threadIdx.x; i < R * (RPAD / 4); i += kThreads) {
-        const int m = i / (RPAD / 4), k4 = (i % (RPAD / 4)) * 4;
-        const float4* mine = reinterpret_cast<const float4*>(&Acc[(q * R + m) * LDA + k4]);
-        float4 v[8];
+      __syncwarp();
+      kb_base += nkb_run;
+      if (it == 0) ptx::pdl_wait();
+      __syncthreads();   // every stage consumed and landed; the ring is free
+      const bool abort = *(volatile int*)&s_abort != 0;
+
+      float* Acc = reinterpret_cast<float*>(smem);
+      float* Ns = reinterpret_cast<float*>(smem + NKG * Sh::ACC);
+      if constexpr (kComp) {
+        // each K group's partial tile into its own slot, then the slots
+        // added in group order into slot 0 (fixed order)
+        if (!abort) {
+          float* mine = Acc + kgrp * (Sh::ACC / 4);
 #pragma unroll
-        for (int s = 0; s < 8; ++s)
-          if (s < S) v[s] = *cluster.map_shared_rank(mine, s);
-        float4 sum = v[0];
+          for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int s = 1; s < 8; ++s)
-          if (s < S) { sum.x += v[s].x; sum.y += v[s].y; sum.z += v[s].z; sum.w += v[s].w; }
-        *reinterpret_cast<float4*>(&Ns[m * LDN + k4]) = sum;
+            for (int t = 0; t < TR; ++t) mine[(rg + 16 * i) * LDA + cgi + GR * t] = acc[i][t];
+        }
+        if (NKG > 1) {
+          asm volatile("bar.sync 2, 256;" ::: "memory");   // the compute warps
+          if (!abort) {
+            for (int q4 = c; q4 < kBM * (RPAD / 4); q4 += 256) {
+              const int m = q4 / (RPAD / 4), k4 = 4 * (q4 % (RPAD / 4));
+              float4 v = *reinterpret_cast<const float4*>(&Acc[m * LDA + k4]);
+#pragma unroll
+              for (int g = 1; g < NKG; ++g) {
+                const float4 w =
+                    *reinterpret_cast<const float4*>(&Acc[g * (Sh::ACC / 4) + m * LDA + k4]);
+                v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
+              }
+              *reinterpret_cast<float4*>(&Acc[m * LDA + k4]) = v;
+            }
+          }
+        }
       }
+      cluster.sync();   // every block's partial tile is in its shared memory
+      if (!abort) {
+        // rows [q R, (q+1) R) of the tile: the S partial tiles summed in rank order
+        for (int i = threadIdx.x; i < R * (RPAD / 4); i += kThreads) {
+          const int m = i / (RPAD / 4), k4 = (i % (RPAD / 4)) * 4;
+          const float4* mine = reinterpret_cast<const float4*>(&Acc[(q * R + m) * LDA + k4]);
+          float4 v[8];
+#pragma unroll
+          for (int s = 0; s < 8; ++s)
+            if (s < S) v[s] = *cluster.map_shared_rank(mine, s);
+          float4 sum = v[0];
+#pragma unroll
+          for (int s = 1; s < 8; ++s)
+            if (s < S) { sum.x += v[s].x; sum.y += v[s].y; sum.z += v[s].z; sum.w += v[s].w; }
+          *reinterpret_cast<float4*>(&Ns[m * LDN + k4]) = sum;
+        }
+      }
+      cluster.sync();   // peers are done reading this block's tile
+      if (!*(volatile int*)&s_abort)
+        tcepi::finish_smem<RPAD, kThreads>(Ns, Os, Ds, a.ep, R, row0, rows);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
     }
-    cluster.sync();   // peers are done reading this block's tile
-    if (!*(volatile int*)&s_abort)
-      tcepi::finish_smem<RPAD, kThreads>(Ns, Os, Ds, a.ep, R, row0, rows);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+  };
+  if (warp < 4) {
+    ptx::setmaxnreg_dec<kRegsWG0>();
+    tiles_loop(std::integral_constant<bool, false>{});
+  } else {
+    ptx::setmaxnreg_inc<kRegsCompute>();
+    tiles_loop(std::integral_constant<bool, true>{});
   }
   if (*(volatile int*)&s_abort && threadIdx.x == 0) atomicExch(a.err, (int)NMF_ETIMEOUT);
 }
@@ -366,13 +430,24 @@ void* f32_ptr() { return reinterpret_cast<void*>(k_stream_f32<RPAD>); }
 
 }  // namespace
 
+// The kernel's register split (setmaxnreg) is sized for a build with
+// kRegsLaunch registers a thread: with any other count the compute
+// warpgroups' increase could wait forever, so such a build is not launched.
+bool f32_regs_ok(void* fn) {
+  cudaFuncAttributes at;
+  if (cudaFuncGetAttributes(&at, fn) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return at.numRegs == kRegsLaunch;
+}
+
 bool f32_kernel_for(int rpad, void** fn, int* smem, int* threads) {
   *threads = kThreads;
   switch (rpad) {
 #define NMF_F32(R) case R: *fn = f32_ptr<R>(); *smem = F32Shape<R>::SMEM; return true;
     NMF_F32(8) NMF_F32(16) NMF_F32(24) NMF_F32(32) NMF_F32(40) NMF_F32(48) NMF_F32(56)
-    NMF_F32(64) NMF_F32(72) NMF_F32(80) NMF_F32(88) NMF_F32(96) NMF_F32(104) NMF_F32(112)
-    NMF_F32(120) NMF_F32(128)
+    NMF_F32(64) NMF_F32(80) NMF_F32(96) NMF_F32(112) NMF_F32(128)
 #undef NMF_F32
   }
   return false;

@@ -614,8 +614,8 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
                    int user_split, TcPlan* plan, std::string* err) {
   TcPlan& pl = *plan;
   pl.prec = prec;
-  // float32 FMA path: ranks padded to 8; tensor cores: N granularity 16
-  pl.rpad = prec == NMF_FP32 ? (int)round_up(r, 8) : rank_pad16(r);
+  // float32 FMA path: ranks padded to 8 (16 above 64); tensor cores: N granularity 16
+  pl.rpad = prec == NMF_FP32 ? rank_pad_f32(r) : rank_pad16(r);
   pl.block_m = kBM;
   // K elements per pipeline stage: 128 bytes, or 64 for split BF16x3 at
   // ranks above 64 (see stage_kbytes)
@@ -632,6 +632,10 @@ nmf_status tc_plan(int prec, const void* X_hi, const void* X_lo, int64_t ldx, co
   const bool have = prec == NMF_FP32 ? f32_kernel_for(pl.rpad, &fn, &smem, &threads)
                                      : kernel_for(prec, pl.rpad, &fn, &smem);
   if (!have) { if (err) *err = "no kernel for this rank"; return NMF_EINVAL; }
+  if (prec == NMF_FP32 && !f32_regs_ok(fn)) {
+    if (err) *err = "the float32 kernel was not built with the register count its warpgroup split needs";
+    return NMF_ECUDA;
+  }
   pl.threads = threads;
   if (prepare_kernel(fn, smem) != cudaSuccess) {
     (void)cudaGetLastError();

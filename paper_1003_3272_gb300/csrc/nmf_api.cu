@@ -358,7 +358,7 @@ nmf_status build_ctx(nmf_ctx* c) {
   c->ld_p = round_up(p, align_el);
   c->plane = (prec == NMF_BF16X3) ? kPlaneBF16x2
              : (prec == NMF_BF16) ? kPlaneBF16 : (prec == NMF_TF32 ? kPlaneTF32 : kPlaneF32);
-  c->rpad = prec == NMF_FP32 ? (int)round_up(r, 8) : rank_pad16(r);
+  c->rpad = prec == NMF_FP32 ? rank_pad_f32(r) : rank_pad16(r);
   {
     // tile-blocked copies (128 rows x 128 bytes per block), zero padded
     const int kbe = bf ? 64 : 32;

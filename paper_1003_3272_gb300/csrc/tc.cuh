@@ -58,6 +58,7 @@ cudaError_t tc_launch(const TcPlan& plan, const EpiArgs& ep, const TcGram& gram,
 
 // The float32 FMA form of the same half step (k_stream_f32.cu).
 bool f32_kernel_for(int rpad, void** fn, int* smem, int* threads);
+bool f32_regs_ok(void* fn);   // built with the register count its split assumes
 cudaError_t f32_launch(const TcPlan& plan, const EpiArgs& ep, const TcGram& gram, int* err,
                        cudaStream_t st);
 

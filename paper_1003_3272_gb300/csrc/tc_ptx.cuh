@@ -217,5 +217,17 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float* va,
   }
 }
 
+
+// Warpgroup register reallocation (all warps of the warpgroup execute it):
+// dec gives registers back to the block's pool, inc waits until the pool
+// holds enough.
+template <int N>
+__device__ __forceinline__ void setmaxnreg_dec() {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N));
+}
+template <int N>
+__device__ __forceinline__ void setmaxnreg_inc() {
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(N));
+}
 }  // namespace ptx
 }  // namespace nmf

@@ -49,6 +49,7 @@ EXPORTS = [
     "nmf_status_str", "nmf_last_error", "nmf_version", "nmf_restart",
     "nmf_kernel_launches", "nmf_profile_enable", "nmf_profile_read", "nmf_gram_noalloc",
     "nmf_selfcheck_div", "nmf_test_expire_next_wait", "nmf_converge", "nmf_qn_run",
+    "nmf_batched_schedule", "nmf_batched_test_expire_next_wait",
     # include/pet.h: penalised PET reconstruction (Section 3.2, Algorithm 2)
     "pet_init", "pet_step", "pet_restart", "pet_objective", "pet_run", "pet_profile_enable",
     "pet_profile_read", "pet_destroy", "pet_last_error",
@@ -92,6 +93,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "nmf_batched_step": ([c_p, ctypes.c_int], ctypes.c_int),
         "nmf_batched_objective": ([c_p, c_p], ctypes.c_int),
         "nmf_batched_destroy": ([c_p], None),
+        "nmf_batched_schedule": ([c_p], ctypes.c_char_p),
+        "nmf_batched_test_expire_next_wait": ([c_p], ctypes.c_int),
         "nmf_status_str": ([ctypes.c_int], ctypes.c_char_p),
         "nmf_last_error": ([c_p], ctypes.c_char_p),
         "nmf_version": ([], ctypes.c_char_p),
@@ -343,6 +346,16 @@ class Batch:
         out = np.empty(self.count, dtype=np.float64)
         _check(self.lib.nmf_batched_objective(self.ctx, out.ctypes.data_as(ctypes.c_void_p)))
         return out
+
+    @property
+    def schedule(self) -> str:
+        """The autotuner's choice, "policy/grid"."""
+        return self.lib.nmf_batched_schedule(self.ctx).decode()
+
+    def expire_next_wait(self):
+        """Test hook: the next iteration's bounded waits run out; the next
+        objective() raises NMFError(ETIMEOUT)."""
+        _check(self.lib.nmf_batched_test_expire_next_wait(self.ctx))
 
     def close(self):
         if getattr(self, "ctx", None):

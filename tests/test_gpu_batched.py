@@ -120,3 +120,78 @@ def test_batched_workload_sample_full_size():
         fo = orc.objective(pr.V, Wo, Ho)
         assert abs(f[b] - fo) / fo <= 1e-5, pr.name
         assert entry_rel_err(out[b][1], Ho)[0] < 5e-5, pr.name
+
+
+def _candidates():
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return [f"{pol}/{g}" for pol in ("lpt", "glpt", "rr")
+            for g in (sms, sms - sms // 8, sms - sms // 4)]
+
+
+@pytest.mark.parametrize("which", range(9))
+def test_every_tuner_candidate_matches_the_oracle(which, monkeypatch):
+    """Each schedule the autotuner may choose (policy x grid), forced through
+    NMF_BATCHED_SCHEDULE, gives the oracle's iterates within the BF16x3 bars;
+    the batch reports the forced choice."""
+    from paper_1003_3272_gb300 import nmf
+    name = _candidates()[which]
+    monkeypatch.setenv("NMF_BATCHED_SCHEDULE", name)
+    probs = _small_batch(10, seed=40 + which)
+    Vs = [to_dev(pr.V) for pr in probs]
+    Ws = [to_dev(pr.W0) for pr in probs]
+    Hs = [to_dev(pr.H0) for pr in probs]
+    b = nmf.Batch(Vs, Ws, Hs, prec="bf16x3")
+    assert b.schedule == name
+    b.step(3)
+    f = b.objective()
+    b.close()
+    for pr, W, H, fg in zip(probs, Ws, Hs, f):
+        Wo, Ho, _, _ = orc.run(pr.V, pr.W0, pr.H0, 3, eps=pr.eps)
+        fo = orc.objective(pr.V, Wo, Ho)
+        assert abs(fg - fo) / fo <= OBJ_BAR["bf16x3"], (name, pr.name)
+        assert entry_rel_err(to_host(W), Wo)[1] <= ENTRY_P99_BAR["bf16x3"], (name, pr.name)
+        assert entry_rel_err(to_host(H), Ho)[1] <= ENTRY_P99_BAR["bf16x3"], (name, pr.name)
+
+
+def test_unknown_forced_schedule_is_rejected(monkeypatch):
+    from paper_1003_3272_gb300 import nmf
+    monkeypatch.setenv("NMF_BATCHED_SCHEDULE", "nosuch/7")
+    probs = _small_batch(2, seed=1)
+    with pytest.raises(nmf.NMFError) as ei:
+        nmf.Batch([to_dev(p.V) for p in probs], [to_dev(p.W0) for p in probs],
+                  [to_dev(p.H0) for p in probs], prec="bf16x3")
+    assert ei.value.status == nmf.EINVAL
+
+
+def test_expired_waits_in_the_grouped_kernel():
+    """Failure detection without a fault: the hook makes every bounded wait
+    of the next iteration run out; no factor changes, the next objective
+    reports NMF_ETIMEOUT, and the batch then runs on exactly as a batch that
+    never had the failed iteration."""
+    import time
+    from paper_1003_3272_gb300 import nmf
+    probs = _small_batch(6, seed=9)
+    ref, fref = _run(probs, 3, "bf16x3")
+    Vs = [to_dev(pr.V) for pr in probs]
+    Ws = [to_dev(pr.W0) for pr in probs]
+    Hs = [to_dev(pr.H0) for pr in probs]
+    b = nmf.Batch(Vs, Ws, Hs, prec="bf16x3")
+    b.step(1)
+    W1, H1 = [to_host(W) for W in Ws], [to_host(H) for H in Hs]
+    b.expire_next_wait()
+    t0 = time.time()
+    b.step(1)
+    with pytest.raises(nmf.NMFError) as ei:
+        b.objective()
+    assert ei.value.status == nmf.ETIMEOUT
+    assert time.time() - t0 < 60
+    for W, H, w1, h1 in zip(Ws, Hs, W1, H1):
+        np.testing.assert_array_equal(to_host(W), w1)
+        np.testing.assert_array_equal(to_host(H), h1)
+    b.step(2)
+    f = b.objective()
+    b.close()
+    assert np.array_equal(f, fref)
+    for (Wr, Hr), W, H in zip(ref, Ws, Hs):
+        assert np.array_equal(to_host(W), Wr) and np.array_equal(to_host(H), Hr)
