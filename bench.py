@@ -453,12 +453,16 @@ def time_batched(prec, steps, warmup, iters, ws, singles=True):
     return out
 
 
-def time_poisson(ws, clocks, steps=3, iters=10):
+def time_poisson_prec(ws, clocks, prec, steps=3, iters=10):
     """The Poisson model of Section 3.1 (simultaneous square-root MM update)
     on the counts workload (8192 x 8192 counts ~ Poisson(W* H*), mean 5,
-    r = 50): iterations/s through nmf_step with the inputs resident, each
-    iteration 8pnr flops on the float32 FMA pipes (b = WH formed once per
-    pass, two passes), against the FFMA peak at the sampled clock."""
+    r = 50) in one precision: iterations/s through nmf_step with the inputs
+    resident.  fp32: 8pnr flops per iteration on the float32 FMA pipes
+    (b = WH formed once per pass, two passes) against the FFMA peak at the
+    sampled clock.  bf16x3: the contractions run on the tensor cores and
+    each iteration streams V twice, 2 x 4pn bytes, against the measured HBM
+    copy bandwidth (the whole iteration's time: both passes and the fused
+    update)."""
     import torch
     from paper_1003_3272_gb300 import nmf, synth
     pr = synth.counts()
@@ -467,7 +471,8 @@ def time_poisson(ws, clocks, steps=3, iters=10):
     W = torch.from_numpy(pr.W0).cuda()
     H = torch.from_numpy(pr.H0).cuda()
     stream = torch.cuda.current_stream()
-    with nmf.NMF(V, W, H, eps=pr.eps, model="poisson", seed=pr.seed, stream=stream) as m:
+    with nmf.NMF(V, W, H, eps=pr.eps, model="poisson", prec=prec, seed=pr.seed,
+                 stream=stream) as m:
         L0 = m.objective()
         m.step(2)
         torch.cuda.synchronize()
@@ -484,23 +489,44 @@ def time_poisson(ws, clocks, steps=3, iters=10):
         m.profile(False)
         L1 = m.objective()
     done = steps * iters
-    flops = 8.0 * p * n * r
     per_it = it_ms / max(1, it_n)
     pk = peaks()
-    mhz = (clocks or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    peak = SMS * FFMA_PER_SM_PER_CLK * 2 * mhz * 1e6 / 1e12
-    achieved = flops / (per_it * 1e-3) / 1e12
+    if prec == "fp32":
+        flops = 8.0 * p * n * r
+        mhz = (clocks or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+        peak = SMS * FFMA_PER_SM_PER_CLK * 2 * mhz * 1e6 / 1e12
+        achieved = flops / (per_it * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "peak_source": "152 SMs x 128 FFMA x 2 x sampled SM clock",
+                "flops_per_iteration": flops}
+    else:
+        nbytes = 2.0 * 4 * p * n
+        achieved = nbytes / (per_it * 1e-3) / 1e9
+        peak = pk["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": round(peak, 1),
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "peak_source": f"{pk['_source']} hbm_gbs (copy bandwidth, MEASURED_PEAKS.json)",
+                "bytes_per_iteration": nbytes}
     del V, W, H
     torch.cuda.empty_cache()
-    return {"workload": synth.COUNTS["name"] + " (counts ~ Poisson(W* H*), mean 5)",
-            "model": "poisson", "precision": "fp32", "iterations": done,
+    return {"precision": prec, "iterations": done,
             "value": round(job_rate(done, ms / 1e3, ws), 1), "unit": "iterations/s",
-            "ms_per_iteration": round(per_it, 4),
-            "roofline": {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1),
-                         "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                         "peak_source": "152 SMs x 128 FFMA x 2 x sampled SM clock",
-                         "flops_per_iteration": flops},
+            "ms_per_iteration": round(per_it, 4), "roofline": roof,
             "loglik_start": L0, "loglik_end": L1}
+
+
+def time_poisson(ws, clocks):
+    """Both forms of the Poisson model on the counts workload, each from the
+    same start for the same number of iterations; the BF16x3 form's
+    loglikelihood is reported relative to the float32 form's."""
+    from paper_1003_3272_gb300 import synth
+    by = {prec: time_poisson_prec(ws, clocks, prec) for prec in ("fp32", "bf16x3")}
+    ref = by["fp32"]["loglik_end"]
+    by["bf16x3"]["loglik_rel_diff_vs_fp32"] = abs(by["bf16x3"]["loglik_end"] - ref) / abs(ref)
+    by["bf16x3"]["speedup_vs_fp32"] = round(by["bf16x3"]["value"] / by["fp32"]["value"], 2)
+    return {"workload": synth.COUNTS["name"] + " (counts ~ Poisson(W* H*), mean 5)",
+            "model": "poisson", "by_precision": by}
 
 
 def pet_stored_objectives(name):

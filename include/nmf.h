@@ -83,7 +83,14 @@ typedef enum {
  *                          H_kj <- H_kj sqrt((sum_i v_ij W_ik / b_ij) / sum_i W_ik)
  *                        with b = W H from the same iteration (eps guards
  *                        the divisions; a term with v_ij = 0 is zero).
- *                        NMF_FP32 and r <= 64 only (else NMF_EUNSUPPORTED);
+ *                        r <= 64, NMF_FP32 (float32 FMA passes) or
+ *                        NMF_BF16X3 (the products W H, q H^T and W^T q of
+ *                        both passes on the tensor cores, split hi + lo with
+ *                        float32 accumulation; nmf_init makes a tile-blocked
+ *                        float32 copy of V, about p n 4 bytes), else
+ *                        NMF_EUNSUPPORTED.  The denominators and the sums of
+ *                        the numerators' segment partials are float64, the
+ *                        final ratio, square root and product float32.
  *                        `order` is ignored; nmf_objective returns L;
  *                        nmf_half_step and nmf_read_gram are not served.  */
 typedef enum {
@@ -269,9 +276,12 @@ nmf_status nmf_gram_noalloc(const float* F, int32_t layout, int64_t M, int64_t l
  * This hook makes that happen on purpose for the next half step: it gives
  * the launch's grid-wide publication waits a target the device counter
  * never reaches, so that every block's wait runs out (about 3 s in all).
- * The context stays usable afterwards.  NMF_EINVAL for ctx == NULL;
- * NMF_EUNSUPPORTED for the Poisson model (its kernels have no grid-wide
- * waits).                                                                  */
+ * For the NMF_BF16X3 Poisson model it acts on the next iteration run by
+ * nmf_step: the first pass's first V stage waits for 16 bytes more than its
+ * copies bring, every block gives up (a few seconds), and the update leaves
+ * W and H unchanged.  The context stays usable afterwards.  NMF_EINVAL for
+ * ctx == NULL; NMF_EUNSUPPORTED for the NMF_FP32 Poisson model (its kernels
+ * have no waits).                                                          */
 nmf_status nmf_test_expire_next_wait(nmf_ctx* ctx);
 
 /* ---- Self-check of the update's division ----------------------------------

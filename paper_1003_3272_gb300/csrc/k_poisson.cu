@@ -313,6 +313,10 @@ k_pois_pass(const float* __restrict__ V, int64_t ldv, const float* __restrict__ 
 }
 
 // Both factors in place: W entries (idx < p r) and H entries (the rest).
+// The numerator's segment partials are summed in float64 (fixed order); the
+// ratio to the denominator, its square root and the product with the old
+// entry are IEEE float32 operations (a few units of 2^-24 in all; float64
+// division and square root are slow on this part and buy nothing here).
 __global__ void k_pois_update(float* __restrict__ W, float* __restrict__ H, int64_t p,
                               int64_t n, int r, float eps, const double* __restrict__ partW,
                               int segW, const double* __restrict__ partH, int segH,
@@ -325,16 +329,16 @@ __global__ void k_pois_update(float* __restrict__ W, float* __restrict__ H, int6
       const int k = (int)(idx - i * r);
       double num = 0.0;
       for (int s = 0; s < segW; ++s) num += partW[((int64_t)s * p + i) * r + k];
-      const double ratio = num / (sums[k] + (double)eps);
-      W[idx] = (float)((double)W[idx] * sqrt(ratio));
+      const float ratio = __fdiv_rn((float)num, (float)(sums[k] + (double)eps));
+      W[idx] = __fmul_rn(W[idx], __fsqrt_rn(ratio));
     } else {
       const int64_t h = idx - nw;
       const int k = (int)(h / n);
       const int64_t j = h - (int64_t)k * n;
       double num = 0.0;
       for (int s = 0; s < segH; ++s) num += partH[((int64_t)s * n + j) * r + k];
-      const double ratio = num / (sums[r + k] + (double)eps);
-      H[h] = (float)((double)H[h] * sqrt(ratio));
+      const float ratio = __fdiv_rn((float)num, (float)(sums[r + k] + (double)eps));
+      H[h] = __fmul_rn(H[h], __fsqrt_rn(ratio));
     }
   }
 }

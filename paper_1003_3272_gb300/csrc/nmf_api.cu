@@ -114,6 +114,8 @@ struct nmf_ctx {
   double* ppartW = nullptr;       // segW x p x r
   double* ppartH = nullptr;       // segH x n x r
   double* pobj_parts = nullptr;   // loglikelihood partials
+  PoisTc* ptc = nullptr;          // NMF_BF16X3: the tensor-core passes (k_pois_tc.cu)
+  bool ptc_expire = false;        // nmf_test_expire_next_wait on the tensor-core passes
   // nmf_qn_run: the quasi-Newton workspace, made on first use for memory q
   int qn_q = 0;
   float* qn_x[3] = {nullptr, nullptr, nullptr};   // x_n, F(x_n), F(F(x_n))
@@ -236,8 +238,9 @@ nmf_status validate_cfg(const nmf_config* cfg) {
     set_err(nullptr, "unknown model");
     return NMF_EINVAL;
   }
-  if (cfg->model == NMF_MODEL_POISSON && (cfg->prec != NMF_FP32 || !pois_supported(cfg->r))) {
-    set_err(nullptr, "the Poisson model is served in NMF_FP32 for ranks 1..64");
+  if (cfg->model == NMF_MODEL_POISSON &&
+      ((cfg->prec != NMF_FP32 && cfg->prec != NMF_BF16X3) || !pois_supported(cfg->r))) {
+    set_err(nullptr, "the Poisson model is served in NMF_FP32 and NMF_BF16X3 for ranks 1..64");
     return NMF_EUNSUPPORTED;
   }
   if (cfg->p > (int64_t)1 << 31 || cfg->n > (int64_t)1 << 31) {
@@ -259,6 +262,10 @@ nmf_status prepare(nmf_ctx* c, bool seed_factors, uint64_t seed) {
       CK(launch_seed_uniform(c->W, p * r, seed, 1, st), "seed W");
       CK(launch_seed_uniform(c->H, (int64_t)r * n, seed, 2, st), "seed H");
       launched(2);
+    }
+    if (c->ptc) {
+      CK(pois_tc_prepare(c->ptc, c->W, c->H, st), "Poisson factor planes");
+      launched(1);
     }
     return NMF_OK;
   }
@@ -309,10 +316,23 @@ nmf_status build_poisson(nmf_ctx* c) {
   const int r = c->r;
   nmf_status s;
   c->pois = true;
-  c->pplan = pois_plan(p, n, r, c->sms);
-  if ((s = dalloc(c, (void**)&c->psums, 2 * (size_t)r * 8)) != NMF_OK) return s;
-  if ((s = dalloc(c, (void**)&c->ppartW, (size_t)c->pplan.segW * p * r * 8)) != NMF_OK) return s;
-  if ((s = dalloc(c, (void**)&c->ppartH, (size_t)c->pplan.segH * n * r * 8)) != NMF_OK) return s;
+  if (c->cfg.prec == NMF_BF16X3) {
+    // the tensor-core form holds its own workspace (blocked V, planes,
+    // partials, denominators)
+    std::string why;
+    c->ptc = pois_tc_create(c->V, p, n, r, c->sms, c->st, &why);
+    if (!c->ptc) {
+      (void)cudaGetLastError();
+      set_err(&c->err, "%s", why.empty() ? "out of host memory" : why.c_str());
+      return why.empty() || why.compare(0, 10, "cudaMalloc") == 0 ? NMF_ENOMEM : NMF_ECUDA;
+    }
+    launched(1);   // the blocked copy of V
+  } else {
+    c->pplan = pois_plan(p, n, r, c->sms);
+    if ((s = dalloc(c, (void**)&c->psums, 2 * (size_t)r * 8)) != NMF_OK) return s;
+    if ((s = dalloc(c, (void**)&c->ppartW, (size_t)c->pplan.segW * p * r * 8)) != NMF_OK) return s;
+    if ((s = dalloc(c, (void**)&c->ppartH, (size_t)c->pplan.segH * n * r * 8)) != NMF_OK) return s;
+  }
   if ((s = dalloc(c, (void**)&c->pobj_parts, (size_t)pois_loglik_parts() * 8)) != NMF_OK) return s;
   if ((s = alloc_common(c)) != NMF_OK) return s;
   return prepare(c, c->cfg.init_from_seed != 0, c->cfg.seed);
@@ -442,6 +462,7 @@ void free_ctx(nmf_ctx* c) {
   if (!c) return;
   if (c->st == nullptr || cudaStreamSynchronize(c->st) != cudaSuccess) (void)cudaDeviceSynchronize();
   for (void* p : c->allocs) cudaFree(p);
+  pois_tc_destroy(c->ptc);
   if (c->f_host) cudaFreeHost(c->f_host);
   if (c->err_host) cudaFreeHost(c->err_host);
   if (c->run_host) cudaFreeHost(c->run_host);
@@ -507,6 +528,16 @@ nmf_status run_half(nmf_ctx* c, int which) {
 
 // One full iteration of the context's model.
 nmf_status run_iteration(nmf_ctx* c) {
+  if (c->ptc) {
+    // the test hook acts on one directly launched iteration, never on a
+    // captured graph
+    const int extra = c->ptc_expire && !c->capturing ? 16 : 0;
+    if (extra) c->ptc_expire = false;
+    CK(pois_tc_iteration(c->ptc, c->W, c->H, c->cfg.eps, c->err_dev, extra, c->st),
+       "Poisson iteration (tensor)");
+    if (!c->capturing) launched(3);
+    return NMF_OK;
+  }
   if (c->pois) {
     CK(pois_iteration(c->pplan, c->V, c->n, c->W, c->H, c->p, c->n, c->r, c->cfg.eps, c->psums,
                       c->ppartW, c->ppartH, c->st), "Poisson iteration");
@@ -716,7 +747,7 @@ nmf_status nmf_converge(nmf_ctx* c, int max_iters, double tol, int check_every,
   if ((s = check_device_error(c)) != NMF_OK) return s;
   const RunState r = *c->run_host;
   // kernels the graph ran: two (Poisson: four) per iteration, two per test
-  launched((c->pois ? 4 : 2) * r.done + 2 * r.checks);
+  launched((c->ptc ? 3 : c->pois ? 4 : 2) * r.done + 2 * r.checks);
   int done = r.done;
   double f = r.f;
   if (!r.stop && done < max_iters) {
@@ -737,6 +768,11 @@ namespace {
 // The factor operand planes from the factors as they are now (after the
 // quasi-Newton loop wrote W and H itself).
 nmf_status refresh_planes(nmf_ctx* c) {
+  if (c->ptc) {
+    CK(pois_tc_prepare(c->ptc, c->W, c->H, c->st), "Poisson factor planes");
+    launched(1);
+    return NMF_OK;
+  }
   if (c->pois) return NMF_OK;
   CK(launch_factor_planes(c->W, kFactorRowMajor, c->p, c->r, c->r, c->Wop_hi, c->Wop_lo,
                           c->ld_p, c->plane, c->st), "W planes");
@@ -989,7 +1025,11 @@ nmf_status nmf_solve(const nmf_config* cfg, const float* V, float* W, float* H, 
 
 nmf_status nmf_test_expire_next_wait(nmf_ctx* c) {
   if (!c) { set_err(nullptr, "ctx is NULL"); return NMF_EINVAL; }
-  if (c->pois) { set_err(&c->err, "the Poisson kernels have no grid-wide waits"); return NMF_EUNSUPPORTED; }
+  if (c->ptc) {
+    c->ptc_expire = true;
+    return NMF_OK;
+  }
+  if (c->pois) { set_err(&c->err, "the NMF_FP32 Poisson kernels have no bounded waits"); return NMF_EUNSUPPORTED; }
   c->gctr_skew = 1ull << 40;   // a counter value no launch reaches
   return NMF_OK;
 }

@@ -61,8 +61,9 @@ def test_config_struct_layout(lib):
 
 @pytest.mark.parametrize("model,prec,r,want", [
     (5, "fp32", 10, "EINVAL"),             # no such model
-    ("poisson", "bf16x3", 10, "EUNSUPPORTED"),   # the Poisson kernels are float32
+    ("poisson", "bf16", 10, "EUNSUPPORTED"),     # fp32 and bf16x3 only
     ("poisson", "tf32", 10, "EUNSUPPORTED"),
+    ("poisson", "bf16x3", 65, "EUNSUPPORTED"),   # the tensor-core form: ranks up to 64
     ("poisson", "fp32", 65, "EUNSUPPORTED"),     # ranks up to 64
 ])
 def test_model_requests_checked_on_the_host(lib, model, prec, r, want):

@@ -143,7 +143,7 @@ def test_requests_the_model_does_not_serve():
     from paper_1003_3272_gb300 import nmf
     pr = synth.counts_problem(100, 120, 8, seed=1)
     with pytest.raises(nmf.NMFError) as ei:
-        _ctx(pr, prec="bf16x3")
+        _ctx(pr, prec="tf32")
     assert ei.value.status == nmf.EUNSUPPORTED
     big = synth.counts_problem(100, 120, 65, seed=1)
     with pytest.raises(nmf.NMFError) as ei:
