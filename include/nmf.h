@@ -88,9 +88,10 @@ typedef enum {
  *                        both passes on the tensor cores, split hi + lo with
  *                        float32 accumulation; nmf_init makes a tile-blocked
  *                        float32 copy of V, about p n 4 bytes), else
- *                        NMF_EUNSUPPORTED.  The denominators and the sums of
- *                        the numerators' segment partials are float64, the
- *                        final ratio, square root and product float32.
+ *                        NMF_EUNSUPPORTED.  NMF_FP32 sums the denominators
+ *                        and the numerators' segment partials in float64,
+ *                        NMF_BF16X3 in compensated float32; the final
+ *                        ratio, square root and product are float32.
  *                        `order` is ignored; nmf_objective returns L;
  *                        nmf_half_step and nmf_read_gram are not served.  */
 typedef enum {

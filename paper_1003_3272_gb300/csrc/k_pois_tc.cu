@@ -507,53 +507,71 @@ struct FParams {
   const int* err;             // set: a pass gave up, the factors stay as they are
   int64_t ldp, ldn, wblocks;
   Planes pl;
-  double* psum;               // [block][64] per-block sums
+  float2* psum;               // [block][64] per-block sums, compensated (sum, correction)
   unsigned* counter;          // last-block counter (zero between launches)
 };
 
+// Kahan's compensated summation (Kahan 1965) in float32: the pair (s, c)
+// carries the running sum and the part of it that rounding dropped.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = __fsub_rn(x, c);
+  const float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
+}
+
 // One block per 64 rows of W (blocks 0 .. wblocks-1) or 64 columns of H
 // (the rest).  The slice is staged in shared memory; with `update`, each
-// entry becomes x sqrt(num / (den + eps)), num the segment partials summed
-// in float64 in segment order, den this iteration's denominator (float32
-// ratio, square root and product, as in the float32 form).  Then the new
-// slice goes to both of its operand planes (coalesced bf16-pair stores; rank
+// entry becomes x sqrt(num / (den + eps)), num the segment partials summed in
+// segment order, den this iteration's denominator (float32 sum, ratio,
+// square root and product, as in the float32 form).  Then the new slice
+// goes to both of its operand planes (coalesced bf16-pair stores; rank
 // entries r .. 63 of the K-major planes as zeros) and its per-rank sums
-// (float64, in order) to psum; the last block to finish sums those in block
-// order into the denominators of the next iteration and rearms the counter
-// (every block has read the old denominators before it counts itself).
+// (compensated float32, in order) to psum; the last block to finish sums
+// those in block order into the denominators of the next iteration and
+// rearms the counter (every block has read the old denominators before it
+// counts itself).  No float64 arithmetic per entry: that pipe is narrow on
+// this part, and the compensated sums carry about twice float32's digits.
 constexpr int kPlT = 64;
-__global__ void __launch_bounds__(256) k_pois_finish(const FParams f) {
+constexpr int kFT = 512;    // threads of k_pois_finish: a few entries each
+constexpr int kFS = kFT / kPlT;   // interleaved runs of the last block's sums
+__global__ void __launch_bounds__(kFT) k_pois_finish(const FParams f) {
   __shared__ float tile[kPlT][kPlT + 1];
-  __shared__ double red[4][kPlT];
+  __shared__ float den[kPlT];
+  __shared__ float2 red[kFS][kPlT];
   __shared__ bool s_last;
   const int tid = threadIdx.x;
   const int r = f.r;
   const bool upd = f.update != 0 && !(f.err != nullptr && *(volatile const int*)f.err != 0);
+  const bool wblock = (int64_t)blockIdx.x < f.wblocks;
+  if (upd && tid < r) den[tid] = (float)(f.sums[wblock ? tid : r + tid] + (double)f.eps);
+  __syncthreads();
   uint32_t h, l;
-  if ((int64_t)blockIdx.x < f.wblocks) {
+  if (wblock) {
     const int64_t i0 = (int64_t)blockIdx.x * kPlT;
     const int rows = (int)(f.p - i0 < kPlT ? f.p - i0 : kPlT);
     // rows i0 .. of W are contiguous, and so are their partials
-    for (int e = tid; e < rows * r; e += 256) {
+    const float* pw = f.partW + i0 * r;
+#pragma unroll 4
+    for (int e = tid; e < rows * r; e += kFT) {
       const int ii = e / r, k = e - ii * r;
       float w = f.W[i0 * r + e];
       if (upd) {
-        double num = 0.0;
-        for (int s = 0; s < f.segW; ++s) num += (double)f.partW[((int64_t)s * f.p + i0) * r + e];
-        const float ratio = __fdiv_rn((float)num, (float)(f.sums[k] + (double)f.eps));
-        w = __fmul_rn(w, __fsqrt_rn(ratio));
+        float num = __ldg(pw + e);
+        for (int s = 1; s < f.segW; ++s) num = __fadd_rn(num, __ldg(pw + (int64_t)s * f.p * r + e));
+        w = __fmul_rn(w, __fsqrt_rn(__fdiv_rn(num, den[k])));
         f.W[i0 * r + e] = w;
       }
       tile[ii][k] = w;
     }
     __syncthreads();
     if (tid < r) {
-      double s = 0.0;
-      for (int ii = 0; ii < rows; ++ii) s += (double)tile[ii][tid];
-      f.psum[(int64_t)blockIdx.x * kPlT + tid] = s;
+      float s = 0.f, c = 0.f;
+      for (int ii = 0; ii < rows; ++ii) kahan_add(s, c, tile[ii][tid]);
+      f.psum[(int64_t)blockIdx.x * kPlT + tid] = make_float2(s, c);
     }
     // Wb: row i, rank pairs (k, k + 1)
-    for (int e = tid; e < rows * 32; e += 256) {
+    for (int e = tid; e < rows * 32; e += kFT) {
       const int ii = e >> 5, k = 2 * (e & 31);
       bf16_split2(k < r ? tile[ii][k] : 0.f, k + 1 < r ? tile[ii][k + 1] : 0.f, h, l);
       const int64_t at = ((i0 + ii) * kPlaneK + k) >> 1;
@@ -562,7 +580,7 @@ __global__ void __launch_bounds__(256) k_pois_finish(const FParams f) {
     }
     // Wt: row k, entry pairs (i, i + 1); i0 and ldp are even, and a pair
     // reaching past p writes a zero into the row's padding (ldp > p then)
-    for (int e = tid; e < r * 32; e += 256) {
+    for (int e = tid; e < r * 32; e += kFT) {
       const int k = e >> 5, ii = 2 * (e & 31);
       if (ii >= rows) continue;
       bf16_split2(tile[ii][k], ii + 1 < rows ? tile[ii + 1][k] : 0.f, h, l);
@@ -573,33 +591,34 @@ __global__ void __launch_bounds__(256) k_pois_finish(const FParams f) {
   } else {
     const int64_t j0 = ((int64_t)blockIdx.x - f.wblocks) * kPlT;
     const int cols = (int)(f.n - j0 < kPlT ? f.n - j0 : kPlT);
-    for (int e = tid; e < r * kPlT; e += 256) {
+    for (int e = tid; e < r * kPlT; e += kFT) {
       const int k = e >> 6, jj = e & 63;
       if (jj < cols) tile[k][jj] = f.H[(int64_t)k * f.n + j0 + jj];
     }
     __syncthreads();
     if (upd) {
       // the partials of columns j0 .. are contiguous ([j][k])
-      for (int e = tid; e < cols * r; e += 256) {
+      const float* ph = f.partH + j0 * r;
+#pragma unroll 4
+      for (int e = tid; e < cols * r; e += kFT) {
         const int jj = e / r, k = e - jj * r;
-        double num = 0.0;
-        for (int s = 0; s < f.segH; ++s) num += (double)f.partH[((int64_t)s * f.n + j0) * r + e];
-        const float ratio = __fdiv_rn((float)num, (float)(f.sums[r + k] + (double)f.eps));
-        tile[k][jj] = __fmul_rn(tile[k][jj], __fsqrt_rn(ratio));
+        float num = __ldg(ph + e);
+        for (int s = 1; s < f.segH; ++s) num = __fadd_rn(num, __ldg(ph + (int64_t)s * f.n * r + e));
+        tile[k][jj] = __fmul_rn(tile[k][jj], __fsqrt_rn(__fdiv_rn(num, den[k])));
       }
       __syncthreads();
-      for (int e = tid; e < r * kPlT; e += 256) {
+      for (int e = tid; e < r * kPlT; e += kFT) {
         const int k = e >> 6, jj = e & 63;
         if (jj < cols) f.H[(int64_t)k * f.n + j0 + jj] = tile[k][jj];
       }
     }
     if (tid < r) {
-      double s = 0.0;
-      for (int jj = 0; jj < cols; ++jj) s += (double)tile[tid][jj];
-      f.psum[(int64_t)blockIdx.x * kPlT + tid] = s;
+      float s = 0.f, c = 0.f;
+      for (int jj = 0; jj < cols; ++jj) kahan_add(s, c, tile[tid][jj]);
+      f.psum[(int64_t)blockIdx.x * kPlT + tid] = make_float2(s, c);
     }
     // Hp: row k, entry pairs (j, j + 1)
-    for (int e = tid; e < r * 32; e += 256) {
+    for (int e = tid; e < r * 32; e += kFT) {
       const int k = e >> 5, jj = 2 * (e & 31);
       if (jj >= cols) continue;
       bf16_split2(tile[k][jj], jj + 1 < cols ? tile[k][jj + 1] : 0.f, h, l);
@@ -608,7 +627,7 @@ __global__ void __launch_bounds__(256) k_pois_finish(const FParams f) {
       reinterpret_cast<uint32_t*>(f.pl.hp[1])[at] = l;
     }
     // Hb: row j, rank pairs (k, k + 1)
-    for (int e = tid; e < cols * 32; e += 256) {
+    for (int e = tid; e < cols * 32; e += kFT) {
       const int jj = e >> 5, k = 2 * (e & 31);
       bf16_split2(k < r ? tile[k][jj] : 0.f, k + 1 < r ? tile[k + 1][jj] : 0.f, h, l);
       const int64_t at = ((j0 + jj) * kPlaneK + k) >> 1;
@@ -616,8 +635,8 @@ __global__ void __launch_bounds__(256) k_pois_finish(const FParams f) {
       reinterpret_cast<uint32_t*>(f.pl.hb[1])[at] = l;
     }
   }
-  // the last block sums the per-block partials, four interleaved runs per
-  // rank then those four in order
+  // the last block sums the per-block partials: kFS interleaved compensated
+  // runs per rank, then those runs in order
   __threadfence();
   __syncthreads();
   if (tid == 0) s_last = atomicAdd(f.counter, 1u) == gridDim.x - 1;
@@ -628,15 +647,24 @@ __global__ void __launch_bounds__(256) k_pois_finish(const FParams f) {
   for (int side = 0; side < 2; ++side) {
     // side 0: row sums of H (blocks wblocks ..), side 1: column sums of W
     const int64_t b0 = side ? 0 : f.wblocks, b1 = side ? f.wblocks : (int64_t)gridDim.x;
-    double s = 0.0;
+    float s = 0.f, c = 0.f;
     if (k < r) {
-#pragma unroll 8
-      for (int64_t b = b0 + sl; b < b1; b += 4) s += __ldcg(f.psum + b * kPlT + k);
+      for (int64_t b = b0 + sl; b < b1; b += kFS) {
+        const float2 x = __ldcg(f.psum + b * kPlT + k);
+        kahan_add(s, c, -x.y);   // a pair (s, c) stands for s - c
+        kahan_add(s, c, x.x);
+      }
     }
-    red[sl][k] = s;
+    red[sl][k] = make_float2(s, c);
     __syncthreads();
-    if (tid < r)
-      f.sums[side ? r + tid : tid] = ((red[0][tid] + red[1][tid]) + red[2][tid]) + red[3][tid];
+    if (tid < r) {
+      float ts = 0.f, tc = 0.f;
+      for (int q = 0; q < kFS; ++q) {
+        kahan_add(ts, tc, -red[q][tid].y);
+        kahan_add(ts, tc, red[q][tid].x);
+      }
+      f.sums[side ? r + tid : tid] = (double)ts - (double)tc;
+    }
     __syncthreads();
   }
   if (tid == 0) *f.counter = 0u;
@@ -733,7 +761,7 @@ struct PoisTc {
   int64_t nkb = 0;             // 32-column blocks per panel (a multiple of 4)
   float* part[2] = {nullptr, nullptr};   // numerator partials of W, H
   double* sums = nullptr;      // 2r denominators
-  double* psum = nullptr;      // per-block denominator partials (k_pois_finish)
+  float2* psum = nullptr;      // per-block denominator partials (k_pois_finish)
   unsigned* counter = nullptr; // its last-block counter (zero between launches)
   int64_t fblocks[2] = {0, 0}; // k_pois_finish blocks over W, over H
   void* buf = nullptr;         // one allocation for all of the above
@@ -787,7 +815,7 @@ PoisTc* pois_tc_create(const float* V, int64_t p, int64_t n, int r, int sms, cud
   const size_t b_pw = al256((size_t)t->segs[0] * p * r * sizeof(float));
   const size_t b_ph = al256((size_t)t->segs[1] * n * r * sizeof(float));
   const size_t b_sums = al256(2 * (size_t)r * sizeof(double));
-  const size_t b_psum = al256((size_t)(t->fblocks[0] + t->fblocks[1]) * kPlT * sizeof(double));
+  const size_t b_psum = al256((size_t)(t->fblocks[0] + t->fblocks[1]) * kPlT * sizeof(float2));
   const size_t total = b_vb + b_planes + b_pw + b_ph + b_sums + b_psum + 256;
   // the copy kernel writes every entry of the blocked V, padding included;
   // the rest starts at zero (plane padding, counter)
@@ -815,7 +843,7 @@ PoisTc* pois_tc_create(const float* V, int64_t p, int64_t n, int r, int sms, cud
   at += b_ph;
   t->sums = reinterpret_cast<double*>(at);
   at += b_sums;
-  t->psum = reinterpret_cast<double*>(at);
+  t->psum = reinterpret_cast<float2*>(at);
   at += b_psum;
   t->counter = reinterpret_cast<unsigned*>(at);
   if (launch_operand_blocked(V, p, n, n, false, 2, t->vb, nullptr, t->nkb, 32, st) !=
@@ -881,7 +909,7 @@ cudaError_t launch_finish(PoisTc* t, float* W, float* H, float eps, int update, 
   f.pl = t->planes;
   f.psum = t->psum;
   f.counter = t->counter;
-  k_pois_finish<<<(unsigned)(t->fblocks[0] + t->fblocks[1]), 256, 0, st>>>(f);
+  k_pois_finish<<<(unsigned)(t->fblocks[0] + t->fblocks[1]), kFT, 0, st>>>(f);
   return cudaGetLastError();
 }
 }  // namespace
