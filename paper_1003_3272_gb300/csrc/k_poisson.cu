@@ -343,13 +343,77 @@ __global__ void k_pois_update(float* __restrict__ W, float* __restrict__ H, int6
   }
 }
 
+// Float-float arithmetic: an unevaluated pair hi + lo of float32 values
+// (about 48 significant bits), on the float32 pipes.  x += (yh + yl), the
+// result renormalised (Dekker 1971).
+__device__ __forceinline__ void ff_add(float& xh, float& xl, float yh, float yl) {
+  float s, e;
+  two_sum(xh, yh, s, e);
+  e = __fadd_rn(e, __fadd_rn(xl, yl));
+  xh = __fadd_rn(s, e);
+  xl = __fsub_rn(e, __fsub_rn(xh, s));
+}
+
+// ln 2 in three parts, the high part with 16 significant bits (Cody and
+// Waite 1980): e * kLn2Hi is exact for every float32 exponent e, and
+// kLn2Hi + kLn2Lo + kLn2Lo2 is ln 2 to about 2^-70.
+constexpr float kLn2Hi = 0.693145751953125f;
+constexpr float kLn2Lo = 1.428606765330187e-06f;
+constexpr float kLn2Lo2 = 5.497923018708371e-14f;
+constexpr int kLnTab = 256;   // ln(1 + k / 256), k = 0 .. 256
+
+// ln(bh + bl) for a normalised float-float pair with bh a positive normal
+// float32, as a float-float pair within about 2^-48 of |ln b| (2^-43 at the
+// largest exponents), by the
+// table-driven reduction of Tang (1990, ACM TOMS 16): bh = 2^e m with m in
+// [1, 2); c = 1 + k / 256 the table point nearest m, so that
+//   ln b = e ln 2 + ln c + ln(1 + r) + ln(1 + bl / bh),  r = (m - c) / c,
+// |r| <= 2^-9; ln(1 + r) = r - r^2 / 2 + r^3 / 3 - r^4 / 4 + r^5 / 5 (the
+// next term is below 2^-56), r and r^2 carried as float-float, the rest in
+// float32; ln(1 + bl / bh) = bl / bh to within 2^-49.  tab holds
+// ln(1 + k / 256) as float-float pairs.
+__device__ __forceinline__ void ln_ff(float bh, float bl, const float2* tab, float& lh,
+                                      float& ll) {
+  const uint32_t u = __float_as_uint(bh);
+  const float ex = (float)((int)(u >> 23) - 127);
+  const float m = __uint_as_float((u & 0x007FFFFFu) | 0x3F800000u);
+  const int k = __float2int_rn(__fmul_rn(__fsub_rn(m, 1.f), (float)kLnTab));
+  const float c = __fadd_rn(1.f, __fmul_rn((float)k, 1.f / (float)kLnTab));   // exact
+  const float d = __fsub_rn(m, c);                                             // exact
+  const float rc = __fdiv_rn(1.f, c);
+  const float rh = __fmul_rn(d, rc);
+  const float rl = __fmul_rn(__fmaf_rn(-rh, c, d), rc);   // the exact remainder / c
+  const float sq = __fmul_rn(rh, rh);
+  const float sqe = __fmaf_rn(rh, rh, -sq);
+  const float tail = __fmul_rn(__fmul_rn(sq, rh),
+                               __fmaf_rn(rh, __fmaf_rn(rh, 0.2f, -0.25f), 1.f / 3.f));
+  const float eh = __fmul_rn(ex, kLn2Lo);
+  const float ehe = __fadd_rn(__fmaf_rn(ex, kLn2Lo, -eh), __fmul_rn(ex, kLn2Lo2));
+  const float2 t = tab[k];
+  // the large parts in float-float, the small ones summed in float32
+  float sh = __fmul_rn(ex, kLn2Hi), sl = 0.f;   // exact
+  ff_add(sh, sl, t.x, 0.f);
+  ff_add(sh, sl, eh, 0.f);
+  ff_add(sh, sl, rh, 0.f);
+  ff_add(sh, sl, __fmul_rn(-0.5f, sq), 0.f);
+  float small = __fadd_rn(__fadd_rn(t.y, ehe), __fadd_rn(rl, __fmul_rn(-0.5f, sqe)));
+  small = __fadd_rn(small, __fadd_rn(__fmul_rn(-rh, rl), tail));
+  small = __fadd_rn(small, __fdiv_rn(bl, bh));
+  ff_add(sh, sl, small, 0.f);
+  lh = sh;
+  ll = sl;
+}
+
 // L = sum_ij [v_ij ln b_ij - b_ij], 0 ln 0 = 0, over 64 x 64 tiles (block b
 // takes tiles b, b + grid, ...; the grid is fixed, so the order is too).
 // b_ij = sum_k w_ik h_kj as an unevaluated float32 pair hi + lo by the
 // compensated dot product of Ogita, Rump and Oishi (2005, "Dot2": exact
 // products by FMA, Knuth's two-sum on the running sum), within a few units
-// of 2^-48 relative of the exact sum; then hi + lo in float64, its float64
-// logarithm and the float64 sum.
+// of 2^-48 relative of the exact sum; ln b by ln_ff; each thread keeps
+// sum v ln b and sum b as float-float pairs, and the thread and block
+// partials are added in float64 in a fixed order.  The float32 pipes carry
+// the per-entry work (the float64 pipe is narrow on this part); entries whose
+// b is not a positive normal float32 take a float64 logarithm instead.
 constexpr int kLBlocks = 2 * 152;
 __global__ void __launch_bounds__(kPThreads)
 k_pois_loglik(const float* __restrict__ V, int64_t ldv, const float* __restrict__ W,
@@ -359,9 +423,18 @@ k_pois_loglik(const float* __restrict__ V, int64_t ldv, const float* __restrict_
   float* Wt = sm;
   float* Hs = sm + r * kLW;
   __shared__ double red[kPThreads];
+  __shared__ float2 lntab[kLnTab + 1];
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  for (int k = tid; k <= kLnTab; k += kPThreads) {
+    const double x = log1p((double)k / kLnTab);
+    const float hi = (float)x;
+    lntab[k] = make_float2(hi, (float)(x - (double)hi));
+  }
   const int64_t tp = (p + kPT - 1) / kPT, tn = (n + kPT - 1) / kPT;
   const bool vec = (ldv % 4 == 0) && (reinterpret_cast<uintptr_t>(V) % 16 == 0);
+  // sum v ln b and sum b as float-float pairs; entries whose b is not a
+  // positive normal float32 (zero, tiny) take the float64 path
+  float vh = 0.f, vl = 0.f, bsh = 0.f, bsl = 0.f;
   double s = 0.0;
   for (int64_t t = blockIdx.x; t < tp * tn; t += gridDim.x) {
     const int64_t i0 = (t / tn) * kPT, j0 = (t % tn) * kPT;
@@ -398,11 +471,23 @@ k_pois_loglik(const float* __restrict__ V, int64_t ldv, const float* __restrict_
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         if (i0 + 4 * ty + a >= p || j0 + 4 * tx + e >= n) continue;
-        const double b = (double)hi[a][e] + (double)lo[a][e];
-        const double x = (double)v[a][e];
-        s += (x != 0.0 ? x * log(b) : 0.0) - b;
+        float bh, bl;
+        two_sum(hi[a][e], lo[a][e], bh, bl);
+        ff_add(bsh, bsl, bh, bl);
+        const float x = v[a][e];
+        if (x == 0.f) continue;
+        if (bh >= 1.17549435e-38f && bh <= 3.4e38f) {
+          float lh, ll;
+          ln_ff(bh, bl, lntab, lh, ll);
+          const float ph = __fmul_rn(x, lh);
+          const float pe = __fmaf_rn(x, lh, -ph);
+          ff_add(vh, vl, ph, __fmaf_rn(x, ll, pe));
+        } else {
+          s += (double)x * log((double)bh + (double)bl);
+        }
       }
   }
+  s += ((double)vh + (double)vl) - ((double)bsh + (double)bsl);
   red[tid] = s;
   __syncthreads();
   for (int w = kPThreads / 2; w >= 1; w >>= 1) {
