@@ -56,7 +56,7 @@
 #include <string>
 
 #include "nmf_internal.cuh"
-#include "tc_ptx.cuh"
+#include "tc_ptx_ta.cuh"
 
 namespace nmf {
 namespace {
