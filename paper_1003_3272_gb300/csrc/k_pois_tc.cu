@@ -10,11 +10,13 @@
 //               into bf16 hi + lo and stored to tensor memory as the A
 //               operand of
 //     MMA2   N_W[i][k] += sum_j q[i][j] H[k][j]          M = 128, N = r, K = 64
-// with N_W in tensor memory for the whole segment (three or four
-// accumulators in rotation, one per tile, so that none takes more than a few
-// hundred additions).  Pass 1 is the same with the roles of the factors
-// swapped (128-column panel J, 64-row tiles I, b^T = H^T W^T, q^T,
-// N_H += q^T W).  Every product is split BF16x3 (hi hi + hi lo + lo hi).  V
+// with N_W in tensor memory for the whole segment.  Pass 1 is the same with
+// the roles of the factors swapped (128-column panel J, 64-row tiles I,
+// b^T = H^T W^T, q^T, N_H += q^T W).  Every product is split BF16x3
+// (hi hi + hi lo + lo hi): per K step, one MMA of A_hi against B's hi and lo
+// planes stacked along N (N = 128, resp. 2 RP) and one of A_lo against B_hi
+// (N = 64, resp. RP) into the first half, so that the result is the sum of
+// the two halves of the accumulator.  V
 // is read once per pass, as float32, from a tile-blocked copy made once when
 // the plan is created: [128-row panel][32-column block][128][32], zero
 // outside V, so that every TMA box is one contiguous piece of HBM (16 KB for
@@ -32,13 +34,13 @@
 // soon as its reader is done with it: V (three stages; freed when the
 // epilogue has read the tile into registers), B1 (the other factor's 64 rows
 // for MMA1, three stages; freed when MMA1 completes) and B2 (the other
-// factor's plane for MMA2, two stages; freed when MMA2 completes); b and q
-// double-buffered in tensor memory.  An M = 128, N = 64 MMA costs the tensor
-// pipe about 45 cycles alone (more while the epilogue's tensor-memory loads
-// and stores run beside it), so a tile's 24 take about as long as its V
-// takes to stream from HBM: MMA1 is issued two tiles ahead of MMA2, so
-// that the MMA thread never waits for the epilogue to finish a tile before
-// giving it the next b.  Every wait is bounded: on expiry the block records
+// factor's plane for MMA2, two stages; freed when MMA2 completes); q
+// double-buffered in tensor memory.  An M = 128 BF16 MMA costs the tensor
+// pipe about 45 cycles at N = 64 and 64 at N = 128, and the one thread that
+// issues them competes for issue slots with the epilogue warps of its
+// sub-partition: the stacked form issues 16 instructions per tile instead of
+// 24.  MMA1 of the next tile is issued as soon as the epilogue has read b,
+// before MMA2 of the current one.  Every wait is bounded: on expiry the block records
 // NMF_ETIMEOUT, stops, waits (bounded) for its copies and MMAs and frees
 // tensor memory.
 //
@@ -74,10 +76,10 @@ constexpr int kNB2 = 2;               // B2 stages
 constexpr uint64_t kWait = 3000ull * 1000 * 1000;   // ~1.5 s at 2 GHz
 
 // Tensor memory (512 columns of 32 bits x 128 lanes):
-//   [0, 128)    b, two buffers of 64 float32 columns
+//   [0, 128)    b: Ahi Bhi + Alo Bhi in [0, 64), Ahi Blo in [64, 128)
 //   [128, 256)  q, two buffers: 32 columns of bf16 pairs hi, then 32 lo
 //   [256, 320)  the panel's factor rows: 32 columns hi, 32 lo
-//   [320, 512)  the numerator accumulators, NACC x RP float32 columns
+//   [320, 320 + 2 RP)  the numerator, in the same two halves
 constexpr int kColB = 0, kColQ = 128, kColA = 256, kColAcc = 320, kTCols = 512;
 
 // Shared memory (bytes), every tile 1024-byte aligned:
@@ -96,8 +98,7 @@ struct PShape {
   static constexpr int OFF_B1 = OFF_V + kNV * VT;
   static constexpr int OFF_B2 = OFF_B1 + kNB1 * B1;
   static constexpr int SMEM = OFF_B2 + kNB2 * B2 + 1024;
-  static constexpr int NACC = RP == 64 ? 3 : 4;   // accumulators in rotation
-  static_assert(kColAcc + NACC * RP <= kTCols, "tensor memory columns");
+  static_assert(kColAcc + 2 * RP <= kTCols, "tensor memory columns");
   static_assert(SMEM <= 232448, "shared memory per block");
   static_assert(B2 % 1024 == 0, "B2 stages stay 1024-byte aligned");
 };
@@ -148,7 +149,6 @@ template <int PASS, int RP>
 __global__ void __launch_bounds__(kPT, 1)
 k_pois_tc(const __grid_constant__ PMaps mp, const PParams a) {
   using Sh = PShape<RP>;
-  constexpr int NACC = Sh::NACC;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t a1_bar;          // A1 landed in shared memory
   __shared__ __align__(8) uint64_t a1_tmem;         // A1 stored to tensor memory
@@ -158,8 +158,8 @@ k_pois_tc(const __grid_constant__ PMaps mp, const PParams a) {
   __shared__ __align__(8) uint64_t b1_empty[kNB1];  // MMA1 complete
   __shared__ __align__(8) uint64_t b2_full[kNB2];
   __shared__ __align__(8) uint64_t b2_empty[kNB2];  // MMA2 complete
-  __shared__ __align__(8) uint64_t bfull[2];        // b ready in TMEM (MMA1 -> epilogue)
-  __shared__ __align__(8) uint64_t bempty[2];       // b read (epilogue -> MMA1)
+  __shared__ __align__(8) uint64_t bfull;           // b ready in TMEM (MMA1 -> epilogue)
+  __shared__ __align__(8) uint64_t bempty;          // b read (epilogue -> MMA1)
   __shared__ __align__(8) uint64_t qfull[2];        // q stored (epilogue -> MMA2)
   __shared__ __align__(8) uint64_t qempty[2];       // q read by MMA2 (MMA2 -> epilogue)
   __shared__ __align__(8) uint64_t done_bar;        // every MMA of this block complete
@@ -196,9 +196,9 @@ k_pois_tc(const __grid_constant__ PMaps mp, const PParams a) {
       ptx::mbar_init(bar(b2_full[s]), 1);
       ptx::mbar_init(bar(b2_empty[s]), 1);
     }
+    ptx::mbar_init(bar(bfull), 1);
+    ptx::mbar_init(bar(bempty), kEpi);
     for (int s = 0; s < 2; ++s) {
-      ptx::mbar_init(bar(bfull[s]), 1);
-      ptx::mbar_init(bar(bempty[s]), kEpi);
       ptx::mbar_init(bar(qfull[s]), kEpi);
       ptx::mbar_init(bar(qempty[s]), 1);
     }
@@ -289,30 +289,30 @@ k_pois_tc(const __grid_constant__ PMaps mp, const PParams a) {
   }
   else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    // MMA1 runs two tiles ahead of MMA2: MMA1 of tile t + 2 goes out as soon
-    // as the epilogue has read b of tile t (its buffer), before MMA2 of tile
-    // t, which needs the epilogue's q of tile t.  MMA2 of tile t goes into
-    // accumulator t % NACC.  Both A operands come from tensor memory.
-    constexpr uint32_t ID1 = ptx::idesc(1, kPM, kPN);
-    constexpr uint32_t ID2 = ptx::idesc(1, kPM, RP);
+    // MMA1 of tile t + 1 goes out as soon as the epilogue has read b of
+    // tile t, before MMA2 of tile t, which needs the epilogue's q of tile t.
+    // Each K step is two instructions: A_hi against B's hi and lo planes
+    // stacked along N, then A_lo against B_hi.  Both A operands come from
+    // tensor memory.
+    constexpr uint32_t ID1W = ptx::idesc(1, kPM, 2 * kPN), ID1N = ptx::idesc(1, kPM, kPN);
+    constexpr uint32_t ID2W = ptx::idesc(1, kPM, 2 * RP), ID2N = ptx::idesc(1, kPM, RP);
     bool ok = ptx::mbar_wait(bar(a1_tmem), 0, kWait);
     ptx::tc_fence_after();
     const uint32_t a1_hi = tmem + (uint32_t)kColA;
     auto mma1 = [&](int t) -> bool {
-      const int s = t & 1, s1 = t % kNB1;
+      const int s1 = t % kNB1;
       if (!ptx::mbar_wait(bar(b1_full[s1]), (uint32_t)(t / kNB1) & 1u, kWait) ||
-          !ptx::mbar_wait(bar(bempty[s]), ((uint32_t)(t >> 1) & 1u) ^ 1u, kWait))
+          !ptx::mbar_wait(bar(bempty), ((uint32_t)t & 1u) ^ 1u, kWait))
         return false;
       ptx::tc_fence_after();
-      const uint64_t dbh = ptx::sdesc_sw128(b1_addr(s1));
-      const uint64_t dbl = ptx::sdesc_sw128(b1_addr(s1) + kPN * 128);
-      const uint32_t tb = tmem + (uint32_t)(kColB + s * kPN);
+      const uint64_t db = ptx::sdesc_sw128(b1_addr(s1));   // hi rows, then lo rows
+      const uint32_t tb = tmem + (uint32_t)kColB;
       // +32 bytes along K per step: +2 in the descriptor's address field
 #pragma unroll
       for (int kk = 0; kk < RP / 16; ++kk)
-        ptx::mma3_ta(tb, a1_hi + 8 * kk, a1_hi + 32 + 8 * kk, dbh + 2 * kk, dbl + 2 * kk, ID1,
-                     kk > 0 ? 1u : 0u);
-      ptx::mma_commit(bar(bfull[s]));
+        ptx::mma2w_ta(tb, a1_hi + 8 * kk, a1_hi + 32 + 8 * kk, db + 2 * kk, ID1W, ID1N,
+                      kk > 0 ? 1u : 0u);
+      ptx::mma_commit(bar(bfull));
       ptx::mma_commit(bar(b1_empty[s1]));
       return true;
     };
@@ -322,22 +322,20 @@ k_pois_tc(const __grid_constant__ PMaps mp, const PParams a) {
           !ptx::mbar_wait(bar(b2_full[s2]), (uint32_t)(t / kNB2) & 1u, kWait))
         return false;
       ptx::tc_fence_after();
-      const uint64_t dhh = ptx::sdesc_sw128(b2_addr(s2));
-      const uint64_t dhl = ptx::sdesc_sw128(b2_addr(s2) + RP * 128);
+      const uint64_t dh = ptx::sdesc_sw128(b2_addr(s2));   // hi rows, then lo rows
       const uint32_t qa = tmem + (uint32_t)(kColQ + 64 * u);
-      const uint32_t td = tmem + (uint32_t)(kColAcc + (t % NACC) * RP);
-      const uint32_t first = t >= NACC ? 1u : 0u;
+      const uint32_t td = tmem + (uint32_t)kColAcc;
 #pragma unroll
       for (int kk = 0; kk < kPN / 16; ++kk)
-        ptx::mma3_ta(td, qa + 8 * kk, qa + 32 + 8 * kk, dhh + 2 * kk, dhl + 2 * kk, ID2,
-                     kk > 0 ? 1u : first);
+        ptx::mma2w_ta(td, qa + 8 * kk, qa + 32 + 8 * kk, dh + 2 * kk, ID2W, ID2N,
+                      (t > 0 || kk > 0) ? 1u : 0u);
       ptx::mma_commit(bar(qempty[u]));       // the q buffer may be rewritten
       ptx::mma_commit(bar(b2_empty[s2]));    // the B2 stage may be refilled
       return true;
     };
-    for (int t = 0; ok && t < nt && t < 2; ++t) ok = mma1(t);
+    if (nt > 0) ok = ok && mma1(0);
     for (int t = 0; ok && t < nt; ++t) {
-      if (t + 2 < nt) ok = mma1(t + 2);
+      if (t + 1 < nt) ok = mma1(t + 1);
       if (ok) ok = mma2(t);
     }
     if (!ok) atomicExch(&s_abort, 1);
@@ -376,14 +374,17 @@ k_pois_tc(const __grid_constant__ PMaps mp, const PParams a) {
       const uint32_t ph = (uint32_t)(t >> 1) & 1u;
       // the V tile landed (TMA) and MMA1 of this tile is complete
       ok = ptx::mbar_wait(bar(v_full[sv]), (uint32_t)(t / kNV) & 1u, kWait) &&
-           ptx::mbar_wait(bar(bfull[s]), ph, kWait);
+           ptx::mbar_wait(bar(bfull), (uint32_t)t & 1u, kWait);
       ok = __all_sync(0xffffffffu, ok);   // tensor-memory accesses are warp-collective
       if (!ok) break;
       ptx::tc_fence_after();
-      float b[kEC];
-      ld_cols(tmem + tl + (uint32_t)(kColB + s * kPN + kEC * cg), b);
+      float b[kEC], bl[kEC];
+      ld_cols(tmem + tl + (uint32_t)(kColB + kEC * cg), b);
+      ld_cols(tmem + tl + (uint32_t)(kColB + kPN + kEC * cg), bl);
       ptx::tc_fence_before();
-      ptx::mbar_arrive(bar(bempty[s]));
+      ptx::mbar_arrive(bar(bempty));
+#pragma unroll
+      for (int e = 0; e < kEC; ++e) b[e] = __fadd_rn(b[e], bl[e]);
       // v at this thread's kEC entries: pass 0 row `row` of the 128 x 64
       // tile, columns kEC cg .. (box of 32 columns kEC cg / 32); pass 1
       // column `row` of the 64 x 128 tile, rows kEC cg .. (box row / 32)
@@ -440,20 +441,18 @@ k_pois_tc(const __grid_constant__ PMaps mp, const PParams a) {
     const bool rd = __all_sync(0xffffffffu, fin && !*(volatile int*)&s_abort);
     const int64_t m = panel * kPM + row;
     float* dst = a.part + ((int64_t)seg * a.rows + m) * a.r;
-    const int used = nt < NACC ? nt : NACC;
 #pragma unroll
     for (int c = 0; c < RP / 16; ++c) {
       if (c % kNG != cg) continue;   // the column groups split the rank chunks
       float sum[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) sum[e] = 0.f;
-      if (rd) {
-        for (int acc = 0; acc < used; ++acc) {
-          float x[16];
-          ptx::tmem_ld16(tmem + tl + (uint32_t)(kColAcc + acc * RP + 16 * c), x);
+      if (rd && nt > 0) {
+        float x[16];
+        ptx::tmem_ld16x2(tmem + tl + (uint32_t)(kColAcc + 16 * c),
+                         tmem + tl + (uint32_t)(kColAcc + RP + 16 * c), sum, x);
 #pragma unroll
-          for (int e = 0; e < 16; ++e) sum[e] = __fadd_rn(sum[e], x[e]);
-        }
+        for (int e = 0; e < 16; ++e) sum[e] = __fadd_rn(sum[e], x[e]);
       }
       if (m < a.rows && rd) {
 #pragma unroll
