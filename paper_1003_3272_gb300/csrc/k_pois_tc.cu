@@ -214,6 +214,10 @@ k_pois_tc(const __grid_constant__ PMaps mp, const PParams a) {
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  // Pass 1 reads nothing pass 0 writes, so pass 0 lets it be scheduled at
+  // once: its blocks take the SMs pass 0 leaves idle, then those pass 0's
+  // blocks free (see the end of the kernel for the other half of this).
+  if (PASS == 0 && threadIdx.x == 0) ptx::pdl_launch_dependents();
   // copies started by this thread (its ring's tiles), for the drain at the end
   int issued = 0;
   bool a1_issued = false;
@@ -479,6 +483,10 @@ k_pois_tc(const __grid_constant__ PMaps mp, const PParams a) {
   __syncthreads();
   if (warp == 1) ptx::tmem_dealloc(tmem, kTCols);
   if (*(volatile int*)&s_abort && threadIdx.x == 0) atomicExch(a.err, (int)NMF_ETIMEOUT);
+  // Pass 1 completes only after pass 0 has: the update launched after it
+  // reads both passes' partials.  (A no-op when not launched as a
+  // programmatic dependent.)
+  if (PASS == 1 && threadIdx.x == 0) ptx::pdl_wait();
 }
 
 // Factor planes for both passes, bf16 hi + lo each (entries of rank >= r and
@@ -753,6 +761,8 @@ struct PoisTc {
   int segs[2] = {1, 1};
   int64_t tiles[2] = {0, 0};
   int smem = 0;
+  int sms = 0;
+  bool overlap = false;        // pass 1 as a programmatic dependent of pass 0
   void* fn[2] = {nullptr, nullptr};
   PMaps maps[2];
   Planes planes{};
@@ -802,6 +812,11 @@ PoisTc* pois_tc_create(const float* V, int64_t p, int64_t n, int r, int sms, cud
     if (sg > t->tiles[ps]) sg = t->tiles[ps];
     t->segs[ps] = (int)sg;
   }
+  // The passes overlap only while pass 0 is one wave (every block resident
+  // from the start): pass 1's blocks wait at their end for pass 0, so they
+  // must never hold SMs that pass 0's later blocks need.
+  t->sms = sms;
+  t->overlap = panels[0] * t->segs[0] <= sms;
   t->fblocks[0] = ceil_div(p, (int64_t)kPlT);
   t->fblocks[1] = ceil_div(n, (int64_t)kPlT);
   // the blocked V: every 128-column panel of pass 1 is four whole blocks
@@ -933,8 +948,18 @@ cudaError_t pois_tc_iteration(PoisTc* t, float* W, float* H, float eps, int* err
     prm.test_extra_tx = ps == 0 ? test_extra_tx : 0;
     const unsigned grid = (unsigned)(ceil_div(prm.rows, (int64_t)kPM) * prm.segs);
     void* args[] = {(void*)&t->maps[ps], (void*)&prm};
-    const cudaError_t e =
-        cudaLaunchKernel(t->fn[ps], dim3(grid), dim3(kPT), args, (size_t)t->smem, st);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(kPT, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)t->smem;
+    cfg.stream = st;
+    // pass 1 as a programmatic dependent of pass 0 (the passes overlap)
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = ps == 1 && t->overlap ? 1 : 0;
+    const cudaError_t e = cudaLaunchKernelExC(&cfg, t->fn[ps], args);
     if (e != cudaSuccess) return e;
   }
   return launch_finish(t, W, H, eps, 1, err, st);
