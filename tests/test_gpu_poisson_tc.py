@@ -69,6 +69,40 @@ def test_one_iteration_matches_oracle(p, n, r, mean):
     assert L1 >= L0
 
 
+@pytest.mark.parametrize("p,n,r", [(1, 9, 1), (7, 1, 1), (2, 3, 2)])
+def test_smallest_shapes(p, n, r):
+    """A single row or column of V: one partial panel and tile per pass."""
+    pr = synth.counts_problem(p, n, r, seed=40 + p + n, mean=6.0)
+    m, W, H = _ctx(pr)
+    with m:
+        m.step(2)
+        W2, H2 = to_host(W), to_host(H)
+    W2o, H2o, _, _ = po.run(pr.V, pr.W0, pr.H0, 2, eps=pr.eps)
+    assert entry_rel_err(W2, W2o)[0] < 2 * ONE_ITER_BAR
+    assert entry_rel_err(H2, H2o)[0] < 2 * ONE_ITER_BAR
+
+
+def test_misaligned_v_equals_aligned():
+    """V as a view that starts 4 bytes into its allocation (not 16-byte
+    aligned, the blocked copy's scalar path): the same iterates, bit for
+    bit, as from an aligned copy."""
+    import torch
+    from paper_1003_3272_gb300 import nmf
+    pr = synth.counts_problem(150, 203, 9, seed=12)
+    base = torch.zeros(pr.p * pr.n + 1, dtype=torch.float32, device="cuda")
+    Vm = base[1:].view(pr.p, pr.n)
+    Vm.copy_(to_dev(pr.V))
+    assert Vm.data_ptr() % 16 != 0
+    outs = []
+    for V in (Vm, to_dev(pr.V)):
+        W, H = to_dev(pr.W0), to_dev(pr.H0)
+        with nmf.NMF(V, W, H, eps=pr.eps, model="poisson", prec="bf16x3") as m:
+            m.step(3)
+            outs.append((to_host(W), to_host(H), m.objective()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2]
+
+
 def test_twenty_iterations_objective_and_iterates():
     pr = synth.counts_problem(257, 392, 12, seed=21, mean=3.0)
     m, W, H = _ctx(pr)
