@@ -254,6 +254,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(const BatchParams a)
     ptx::mma_commit(ptx::smem_u32(&done_bar));
   } else if (warp >= 2) {
     // ---------------- epilogue warps (128 threads) ----------------
+    // Per item: the instance's Gram G and the row's old factor values are
+    // read, and den = old . G + eps formed, while the item is still being
+    // streamed; only the quotient old * num / den waits for the accumulator.
+    // den accumulates all ranks k at once (32 independent chains, G read as
+    // broadcast float4 rows), in the same order over l as a plain dot product.
     const int et = threadIdx.x - 64;
     const int quarter = warp & 3;                 // TMEM lanes 32 * (warp % 4)
     const int row = quarter * 32 + lane;
@@ -264,14 +269,39 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(const BatchParams a)
       const int2 it = a.items[i];
       const BatchInst& B = a.inst[it.x];
       const int r = B.r;
-      // the instance's Gram (kBR x kBR) into shared memory
-      epi_sync();
+      const int64_t M = B.M[half];
+      const int64_t m = (int64_t)it.y * kBM + row;
+      const bool live = m < M;
+      float* F = B.F[half];
+      const int64_t ldf = B.ldf[half];
+      epi_sync();                                 // Gs and Vs free (previous item done)
       {
         float gv[kBR * kBR / 128];
 #pragma unroll
         for (int j = 0; j < kBR * kBR / 128; ++j) gv[j] = __ldcg(B.Gpad[half] + et + 128 * j);
 #pragma unroll
         for (int j = 0; j < kBR * kBR / 128; ++j) Gs[et + 128 * j] = gv[j];
+      }
+      float old[kBR];
+#pragma unroll
+      for (int k = 0; k < kBR; ++k)
+        old[k] = (live && k < r) ? (half == 0 ? F[(int64_t)k * ldf + m] : F[m * ldf + k]) : 0.f;
+      epi_sync();                                 // Gs complete
+      float den[kBR];
+#pragma unroll
+      for (int k = 0; k < kBR; ++k) den[k] = 0.f;
+#pragma unroll
+      for (int l = 0; l < kBR; ++l) {
+        if (l >= r) break;
+        const float4* gl = reinterpret_cast<const float4*>(Gs + l * kBR);
+#pragma unroll
+        for (int q = 0; q < kBR / 4; ++q) {
+          const float4 g = gl[q];
+          den[4 * q + 0] = fmaf(old[l], g.x, den[4 * q + 0]);
+          den[4 * q + 1] = fmaf(old[l], g.y, den[4 * q + 1]);
+          den[4 * q + 2] = fmaf(old[l], g.z, den[4 * q + 2]);
+          den[4 * q + 3] = fmaf(old[l], g.w, den[4 * q + 3]);
+        }
       }
       bool ok = ptx::mbar_wait(ptx::smem_u32(&accf[buf]), use & 1u, kWaitCycles);
       ok = __all_sync(0xffffffffu, ok);   // tensor-memory loads are warp-collective
@@ -286,41 +316,56 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(const BatchParams a)
       }
       ptx::tc_fence_before();
       ptx::mbar_arrive(ptx::smem_u32(&acce[buf]));
-      // Gs complete; an expired wait anywhere stops every epilogue thread alike
+      // an expired wait anywhere stops every epilogue thread alike
       if (epi_sync_or(*(volatile int*)&s_abort != 0)) break;
-      const int64_t M = B.M[half];
-      const int64_t m = (int64_t)it.y * kBM + row;
-      float* vrow = Vs + row * Sh::VLD;
+      // The quotients first (independent, eight ranks at a time), then the
+      // stores: H's columns and both planes directly (consecutive rows m are
+      // consecutive addresses), W's rows through Vs below (the item's rows of
+      // the row-major W are one contiguous block).
+      float v[kBR];
 #pragma unroll
-      for (int k = 0; k < kBR; k += 4)
-        *reinterpret_cast<float4*>(vrow + k) = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (m < M) {
-        float old[kBR];
-        float* F = B.F[half];
-        const int64_t ldf = B.ldf[half];
+      for (int k = 0; k < kBR; ++k) v[k] = 0.f;
+      if (live) {
 #pragma unroll
-        for (int k = 0; k < kBR; ++k)
-          old[k] = k < r ? (half == 0 ? F[(int64_t)k * ldf + m] : F[m * ldf + k]) : 0.f;
+        for (int k0 = 0; k0 < kBR; k0 += 8) {
+          if (k0 >= r) break;
+#pragma unroll
+          for (int k = k0; k < k0 + 8; ++k) {
+            const bool in = k < r;
+            v[k] = div_rn(in ? __fmul_rn(old[k], num[k]) : 0.f, in ? __fadd_rn(den[k], B.eps) : 1.f);
+          }
+        }
 #pragma unroll
         for (int k = 0; k < kBR; ++k) {
           if (k >= r) break;
-          float den = 0.f;
-#pragma unroll
-          for (int l = 0; l < kBR; ++l)
-            if (l < r) den = fmaf(old[l], Gs[l * kBR + k], den);
-          den = __fadd_rn(den, B.eps);
-          const float v = div_rn(__fmul_rn(old[k], num[k]), den);
-          if (half == 0) F[(int64_t)k * ldf + m] = v;
-          else           F[m * ldf + k] = v;
-          plane_store(B.plane, B.op_hi[half], B.op_lo[half], (int64_t)k * B.ldop[half] + m, v);
-          vrow[k] = v;
+          if (half == 0) F[(int64_t)k * ldf + m] = v[k];
+          plane_store(B.plane, B.op_hi[half], B.op_lo[half], (int64_t)k * B.ldop[half] + m, v[k]);
         }
       }
+      float* vrow = Vs + row * Sh::VLD;
+#pragma unroll
+      for (int k = 0; k < kBR; k += 4)
+        *reinterpret_cast<float4*>(vrow + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
       // Gram of the item's new rows (float32 over its 128 rows): two groups of
       // 64 threads take 64 rows each, one 4 x 4 block of the 32 x 32 per
       // thread; group 1's sums go through Gs (free until the next item),
       // group 0 adds them and stores the float64 result in the item's slot.
       epi_sync();
+      if (half == 1) {
+        // W's new rows m0 .. m0 + rows - 1 (row-major, ldf = r): one
+        // contiguous block, copied from Vs with consecutive threads on
+        // consecutive addresses
+        const int64_t m0 = (int64_t)it.y * kBM;
+        const int total = (int)(M - m0 < kBM ? M - m0 : (int64_t)kBM) * r;
+        const int dq = kBM / r, dr = kBM % r;
+        int rw = et / r, cl = et % r;
+        for (int e = et; e < total; e += kBM) {
+          F[(m0 + rw) * ldf + cl] = Vs[rw * Sh::VLD + cl];
+          rw += dq;
+          cl += dr;
+          if (cl >= r) { cl -= r; ++rw; }
+        }
+      }
       {
         const int grp = et >> 6, bi = (et >> 3) & 7, bj = et & 7;
         float acc[4][4];
