@@ -649,9 +649,30 @@ def time_converge(ws, prec="fp32", tol=1e-9, max_iters=100000):
                        "iters_per_s": round(done * ws / te, 1), "objective": f,
                        "first_call_ms": round(tb * 1e3, 2)}
     a, b = finals["converge"], finals["run"]
+    resident = None
+    if prec == "fp32":
+        # every iteration in one persistent launch (nmf_converge_resident):
+        # float32 rounding differs from the streaming kernels', so its count
+        # and objective are reported beside the device loop's
+        V = torch.from_numpy(pr.V).cuda()
+        W = torch.from_numpy(pr.W0).cuda()
+        H = torch.from_numpy(pr.H0).cuda()
+        with nmf.NMF(V, W, H, eps=pr.eps, prec=prec) as m:
+            m.converge_resident(1, tol=tol, check_every=1)
+            m.restart(synth.BASE_SEED)
+            torch.cuda.synchronize()
+            barrier(ws)
+            t0 = time.perf_counter()
+            done, f = m.converge_resident(max_iters, tol=tol, check_every=1)
+            te = max_over_ranks(time.perf_counter() - t0, ws)
+        resident = {"iterations": done, "seconds": round(te, 4),
+                    "iters_per_s": round(done * ws / te, 1), "objective": f,
+                    "rel_objective_diff_vs_device_loop": float(f"{abs(f - a[1]) / a[1]:.3e}"),
+                    "over_device_loop": round(res["converge"]["seconds"] / te, 2)}
     return {"workload": "faces_361x2429_r10 (seeded start from nmf_restart)",
             "precision": prec, "tol": tol, "max_iters": max_iters, "check_every": 1,
             "device_loop": res["converge"], "host_loop": res["run"],
+            "resident": resident,
             "device_over_host": round(res["run"]["seconds"] / res["converge"]["seconds"], 3),
             "identical_results": bool(a[0] == b[0] and a[1] == b[1]
                                       and np.array_equal(a[2], b[2])
@@ -698,6 +719,7 @@ def time_workloads(ws, local, clocks, tall_ranks=(16, 32, 64, 128)):
     all4 = ["fp32", "tf32", "bf16x3", "bf16"]
     pr = synth.faces()
     out[pr.name] = run(pr, all4, pr.name)
+    out[pr.name]["resident_fp32"] = time_resident(pr, ws)
     base = synth.tall(tall_ranks[0])
     for r in tall_ranks:
         W0, H0 = synth.starting_factors(base.seed, base.p, base.n, r)
@@ -708,6 +730,36 @@ def time_workloads(ws, local, clocks, tall_ranks=(16, 32, 64, 128)):
     out[pr.name] = run(pr, ["fp32", "bf16x3"], pr.name)
     del pr
     return out
+
+
+def time_resident(pr, ws, reps=5):
+    """A small workload's iterations through nmf_converge_resident (one
+    persistent launch; tol = 0, one objective at the end), FP32: the median
+    wall time of `reps` calls from the seeded start, the call's whole cost
+    (the starting objective, the launch, the final synchronisation)."""
+    import torch
+    from paper_1003_3272_gb300 import nmf
+    V = torch.from_numpy(pr.V).cuda()
+    W = torch.from_numpy(pr.W0).cuda()
+    H = torch.from_numpy(pr.H0).cuda()
+    W0, H0 = W.clone(), H.clone()
+    times = []
+    with nmf.NMF(V, W, H, eps=pr.eps) as m:
+        m.converge_resident(pr.iters, tol=0.0, check_every=pr.iters)
+        for _ in range(reps):
+            W.copy_(W0)
+            H.copy_(H0)
+            torch.cuda.synchronize()
+            barrier(ws)
+            t0 = time.perf_counter()
+            done, f = m.converge_resident(pr.iters, tol=0.0, check_every=pr.iters)
+            times.append(max_over_ranks(time.perf_counter() - t0, ws))
+    t = sorted(times)[len(times) // 2]
+    acc = accuracy(pr.name, pr.iters, {"fp32": f})
+    e = acc.get("rel_objective_error_vs_fp64_oracle")
+    return {"updates_per_s": round(done * ws / t, 1), "ms_per_step": round(t * 1e3, 3),
+            "api": "nmf_converge_resident (one persistent launch, wall time of the call)",
+            "rel_objective_error_vs_fp64_oracle": e.get("fp32") if e else None}
 
 
 def oracle_objective(workload, iters):

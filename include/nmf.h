@@ -173,6 +173,30 @@ nmf_status nmf_run(nmf_ctx* ctx, int max_iters, double tol, int check_every,
 nmf_status nmf_converge(nmf_ctx* ctx, int max_iters, double tol, int check_every,
                         int* iters_done, double* f_out);
 
+/* nmf_converge with every iteration in ONE persistent launch, for problems
+ * that are launch-bound rather than HBM-bound (the faces matrix of the
+ * paper's Table 2, 361 x 2429): Algorithm 1 (Eqs. (3.3)-(3.4)) in cfg.order
+ * and Section 3's stopping rule on Eq. (3.1)'s objective, with the same
+ * arguments, rounds of `check_every` iterations, remainder and results
+ * (*iters_done, *f_out) as nmf_converge.  One cooperative launch of one block
+ * per SM: each block keeps a column slice of V and a row slice of V in shared
+ * memory for the whole run, updates its columns of H and its rows of W
+ * (reading the whole other factor each half step), and the blocks meet at a
+ * grid-wide barrier after every half step; the objective of a round is a
+ * float64 sum of per-block partials in block order, so every block takes the
+ * same stopping decision.  Arithmetic: float32 products and Grams with fixed
+ * reduction trees, IEEE division, compensated float32 residuals summed in
+ * float64; the iterates agree with nmf_converge's to float32 rounding, not
+ * bitwise.  Needs NMF_MODEL_GAUSSIAN and NMF_FP32 (else NMF_EUNSUPPORTED),
+ * r <= 16, and V's two slices plus the larger factor within one block's
+ * shared memory (else NMF_EUNSUPPORTED; 361 x 2429 fits up to r = 12).  A
+ * workspace of (p + n) * ceil4(r) floats is allocated on the first
+ * call.  A grid-wide barrier that waits longer than about a second makes
+ * the call return NMF_ETIMEOUT.  Afterwards the other entry points continue
+ * from the new W and H.  Synchronises.                                      */
+nmf_status nmf_converge_resident(nmf_ctx* ctx, int max_iters, double tol, int check_every,
+                                 int* iters_done, double* f_out);
+
 /* Quasi-Newton acceleration of the MM map (the scheme the paper names in
  * Section 4; Zhou, Alexander & Lange).  Each iteration evaluates
  * x1 = F(x_n) and x2 = F(x1) by two MM iterations (F = nmf_step(ctx, 1); x

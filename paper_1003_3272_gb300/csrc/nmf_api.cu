@@ -134,6 +134,10 @@ struct nmf_ctx {
   RunState* run_dev = nullptr;
   RunState* run_host = nullptr;   // pinned
   cudaStream_t cap_st = nullptr;  // private stream the loop body is captured on
+  // nmf_converge_resident: padded factor copies, objective partials, barrier
+  float* res_work = nullptr;
+  double* res_fpart = nullptr;
+  unsigned long long* res_bar = nullptr;
   cudaGraphExec_t conv_exec = nullptr;
   int conv_k = 0;
   std::vector<cudaEvent_t> ev_pool;
@@ -758,6 +762,61 @@ nmf_status nmf_converge(nmf_ctx* c, int max_iters, double tol, int check_every,
   }
   if (iters_done) *iters_done = done;
   if (f_out) *f_out = f;
+  return NMF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+nmf_status refresh_planes(nmf_ctx* c);
+}  // namespace
+
+extern "C" {
+
+nmf_status nmf_converge_resident(nmf_ctx* c, int max_iters, double tol, int check_every,
+                                 int* iters_done, double* f_out) {
+  if (!c) { set_err(nullptr, "ctx is NULL"); return NMF_EINVAL; }
+  if (max_iters < 0 || check_every < 1 || !(tol >= 0.0)) {
+    set_err(&c->err, "need max_iters >= 0, check_every >= 1, tol >= 0");
+    return NMF_EINVAL;
+  }
+  if (c->pois || c->cfg.prec != NMF_FP32) {
+    set_err(&c->err, "the resident form runs the Gaussian model in NMF_FP32");
+    return NMF_EUNSUPPORTED;
+  }
+  int dev = 0, optin = 0;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attribute");
+  if (!resident_supported(c->p, c->n, c->r, c->sms, (size_t)optin)) {
+    set_err(&c->err, "the resident form needs r <= %d and V's slices and a factor within one "
+                     "block's shared memory (p = %lld, n = %lld, r = %d)",
+            kResidentMaxRank, (long long)c->p, (long long)c->n, c->r);
+    return NMF_EUNSUPPORTED;
+  }
+  nmf_status s = NMF_OK;
+  if (!c->res_work) {
+    if ((s = dalloc(c, (void**)&c->res_work,
+                    resident_workspace_floats(c->p, c->n, c->r) * sizeof(float))) != NMF_OK ||
+        (s = dalloc(c, (void**)&c->res_fpart, sizeof(double) * (size_t)c->sms)) != NMF_OK ||
+        (s = dalloc(c, (void**)&c->res_bar, sizeof(unsigned long long))) != NMF_OK)
+      return s;
+  }
+  CK(launch_model_objective(c), "objective");
+  CK(launch_resident(c->V, c->W, c->H, c->p, c->n, c->r, c->cfg.eps,
+                     c->cfg.order == NMF_ORDER_H_FIRST, max_iters, check_every, tol, c->f_dev,
+                     c->res_work, c->res_fpart, c->res_bar, c->err_dev, c->run_dev, c->sms,
+                     c->st), "resident launch");
+  launched(2);
+  CK(cudaMemcpyAsync(c->run_host, c->run_dev, sizeof(RunState), cudaMemcpyDeviceToHost, c->st),
+     "memcpy run state");
+  if ((s = check_device_error(c)) != NMF_OK) return s;
+  const RunState r = *c->run_host;
+  // the streaming forms' operand planes and Grams from the new factors
+  if ((s = refresh_planes(c)) != NMF_OK || (s = reduce_gram(c, 0)) != NMF_OK ||
+      (s = reduce_gram(c, 1)) != NMF_OK)
+    return s;
+  if (iters_done) *iters_done = r.done;
+  if (f_out) *f_out = r.f;
   return NMF_OK;
 }
 

@@ -49,6 +49,7 @@ EXPORTS = [
     "nmf_status_str", "nmf_last_error", "nmf_version", "nmf_restart",
     "nmf_kernel_launches", "nmf_profile_enable", "nmf_profile_read", "nmf_gram_noalloc",
     "nmf_selfcheck_div", "nmf_test_expire_next_wait", "nmf_converge", "nmf_qn_run",
+    "nmf_converge_resident",
     "nmf_batched_schedule", "nmf_batched_test_expire_next_wait",
     # include/pet.h: penalised PET reconstruction (Section 3.2, Algorithm 2)
     "pet_init", "pet_step", "pet_restart", "pet_objective", "pet_run", "pet_profile_enable",
@@ -81,6 +82,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "nmf_converge": ([c_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)],
                          ctypes.c_int),
+        "nmf_converge_resident": ([c_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)],
+                                  ctypes.c_int),
         "nmf_qn_run": ([c_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                         ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -232,6 +236,16 @@ class NMF:
         done, f = ctypes.c_int(), ctypes.c_double()
         _check(self.lib.nmf_converge(self.ctx, int(max_iters), float(tol), int(check_every),
                                      ctypes.byref(done), ctypes.byref(f)), self.ctx)
+        return done.value, f.value
+
+    def converge_resident(self, max_iters: int, tol: float = 1e-9, check_every: int = 1):
+        """converge() with every iteration in one persistent launch (small
+        problems, NMF_FP32, r <= 16; see nmf_converge_resident).  Same rule
+        and return values; float32 rounding differs from converge()."""
+        done, f = ctypes.c_int(), ctypes.c_double()
+        _check(self.lib.nmf_converge_resident(self.ctx, int(max_iters), float(tol),
+                                              int(check_every), ctypes.byref(done),
+                                              ctypes.byref(f)), self.ctx)
         return done.value, f.value
 
     def qn_run(self, q: int, max_iters: int, tol: float = 0.0):
