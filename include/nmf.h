@@ -184,16 +184,18 @@ nmf_status nmf_converge(nmf_ctx* ctx, int max_iters, double tol, int check_every
  * (reading the whole other factor each half step), and the blocks meet at a
  * grid-wide barrier after every half step; the objective of a round is a
  * float64 sum of per-block partials in block order, so every block takes the
- * same stopping decision.  Arithmetic: float32 products and Grams with fixed
- * reduction trees, IEEE division, compensated float32 residuals summed in
- * float64; the iterates agree with nmf_converge's to float32 rounding, not
- * bitwise.  Needs NMF_MODEL_GAUSSIAN and NMF_FP32 (else NMF_EUNSUPPORTED),
- * r <= 16, and V's two slices plus the larger factor within one block's
- * shared memory (else NMF_EUNSUPPORTED; 361 x 2429 fits up to r = 12).  A
- * workspace of (p + n) * ceil4(r) floats is allocated on the first
- * call.  A grid-wide barrier that waits longer than about a second makes
- * the call return NMF_ETIMEOUT.  Afterwards the other entry points continue
- * from the new W and H.  Synchronises.                                      */
+ * same stopping decision.  Arithmetic: float32 products with fixed reduction
+ * trees, each Gram the float32 sum in block order of the blocks' partial
+ * Grams of their own slices, IEEE division, compensated float32 residuals
+ * summed in float64; the iterates agree with nmf_converge's to float32
+ * rounding, not bitwise.  Needs NMF_MODEL_GAUSSIAN and NMF_FP32 (else
+ * NMF_EUNSUPPORTED), r <= 16, and V's two slices plus the larger factor
+ * within one block's shared memory (else NMF_EUNSUPPORTED; 361 x 2429 fits
+ * up to r = 12).  A workspace of (p + n) * ceil4(r) + sms * r * (r + 1)
+ * floats is allocated on the first call.  A grid-wide barrier that waits
+ * longer than about a second makes the call return NMF_ETIMEOUT.
+ * Afterwards the other entry points continue from the new W and H.
+ * Synchronises.                                                             */
 nmf_status nmf_converge_resident(nmf_ctx* ctx, int max_iters, double tol, int check_every,
                                  int* iters_done, double* f_out);
 

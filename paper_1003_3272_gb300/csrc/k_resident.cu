@@ -12,16 +12,19 @@
 //      (asynchronous 16-byte copies of a padded [K][RP] copy of each factor
 //      that the kernel keeps beside W and H), the block's own old columns O
 //      of H;
-//   2. one small contraction C = Ys^T [X | Ys] over K = p: the numerators
-//      (W^T V)[k][j] for the block's columns j and the Gram W^T W, in float32
-//      (each thread a K segment and four output columns; the segments are
-//      summed in a fixed xor tree within a warp, then the warps in order);
-//   3. den = O G + eps and new = O * num / den (IEEE division), written to H
-//      and to the padded copy;
-//   4. when the half step ends a round, the block's part of
+//   2. the Gram W^T W as the sum, in block order, of the partial Grams that
+//      every block left for its own rows of W (upper triangle, float32);
+//   3. the numerators (W^T V)[k][j] for the block's columns j as one small
+//      contraction Ys^T X over K = p in float32 (each thread a 4 x 4 tile of
+//      one K segment; the segments summed by a fixed xor tree within a warp,
+//      then warp by warp in order);
+//   4. den = O G + eps and new = O * num / den (IEEE division), written to H
+//      and to the padded copy, and the partial Gram of the block's new
+//      columns for the next half step;
+//   5. when the half step ends a round, the block's part of
 //      ||V - W H||_F^2 over its slice (compensated float32 dot products,
 //      float64 sums) into its partial slot;
-//   5. a grid-wide barrier (a counter with bounded waits).
+//   6. a grid-wide barrier (a counter with bounded waits).
 // After each round every block sums the objective partials in block order,
 // so all blocks take the same stopping decision.
 #include <cooperative_groups.h>
@@ -35,7 +38,7 @@ namespace {
 
 constexpr int kRT = 512;                 // threads per block
 constexpr int kRW = kRT / 32;            // warps per block
-constexpr int kMaxGroups = 8;            // output groups of four columns
+constexpr int kMaxTasks = 32;            // 4 x 4 numerator tiles of a half step
 constexpr long long kBarCycles = 2000000000LL;   // a grid barrier waits at most ~1 s
 
 struct ResArgs {
@@ -44,7 +47,9 @@ struct ResArgs {
   float* H;
   float* Wp;              // p x RP, rows 16-byte aligned, columns >= r zero
   float* Hp;              // n x RP (H transposed), the same layout
-  int p, n, r;
+  float* gpW;             // [grid][E] partial Grams of W over each block's rows
+  float* gpH;             // [grid][E] partial Grams of H over each block's columns
+  int p, n, r, E;         // E = r (r + 1) / 2 entries of an upper triangle
   float eps;
   int h_first;
   int max_iters, check_every;
@@ -61,17 +66,20 @@ struct ResArgs {
 template <int RP>
 struct ResSmem {
   // float offsets into the dynamic shared memory
-  int xc, xr, ys, o, on, c, red, total;
+  int xc, xr, ys, o, on, num, gr, sg, red, total, ldn;
   __host__ __device__ ResSmem(int p, int n, int ldc, int ldr, int mnm) {
     const int mnm4 = (mnm + 3) & ~3;
+    ldn = mnm4;
     xc = 0;
     xr = xc + p * ldc;
     ys = xr + n * ldr;
     o = ys + (p > n ? p : n) * RP;
     on = o + mnm4 * RP;
-    c = on + mnm4 * RP;
-    red = c + kMaxGroups * RP * 4;
-    total = red + kRW * kMaxGroups * RP * 4;
+    num = on + mnm4 * RP;        // NUM[k][m], RP x mnm4
+    gr = num + RP * mnm4;        // the Gram, RP x RP (zero beyond r)
+    sg = gr + RP * RP;           // chunk sums of the partial Grams (<= kRT)
+    red = sg + kRT;
+    total = red + kRW * kMaxTasks * 16;
   }
 };
 
@@ -95,8 +103,9 @@ __device__ bool grid_barrier(unsigned long long* bar, unsigned long long idx, in
                              int* s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(bar, 1ull);
+    // release: this block's writes (ordered before by the block barrier)
+    // are visible to whoever acquires the counter
+    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(bar) : "memory");
     const unsigned long long target = (idx + 1) * (unsigned long long)gridDim.x;
     const long long t0 = clock64();
     int ok = 1;
@@ -106,74 +115,119 @@ __device__ bool grid_barrier(unsigned long long* bar, unsigned long long idx, in
         atomicExch(err, 3);
         break;
       }
-      __nanosleep(32);
     }
-    __threadfence();
     *s_ok = ok;
   }
   __syncthreads();
   return *s_ok != 0;
 }
 
-// C[g][a][c] = sum over K of Ys[K][a] * Z_g[K][c] for the groups g of four
-// output columns: g < gx the columns 4g.. of X ([K][ldx]), g >= gx the
-// columns 4(g - gx).. of Ys itself (the Gram).  Thread t takes group
-// t % ngp and the K segment t / ngp; segments are summed by an xor tree over
-// the lanes of a warp, then warp by warp in order.
+// NUM[k][m] = sum over K of Ys[K][k] * X[K][m] (k < RP, m < 4 gx): the
+// tasks are the 4 x 4 tiles (k block a4, m block g); thread t takes task
+// t % ntp and the K segment t / ntp; the segments are summed by an xor tree
+// over the lanes of a warp that share a task, then warp by warp in order.
 template <int RP>
-__device__ void contract(const float* X, int ldx, int gx, const float* Ys, int K, float* Red,
-                         float* C) {
-  constexpr int GY = RP / 4;
-  const int ng = gx + GY;
-  int ngp = 1;
-  while (ngp < ng) ngp <<= 1;
-  const int t = threadIdx.x, g = t % ngp, s = t / ngp, nseg = kRT / ngp;
+__device__ void contract_num(const float* X, int ldx, int gx, const float* Ys, int K,
+                             float* Red, float* NUM, int ldn) {
+  const int ntask = (RP / 4) * gx;
+  int ntp = 1;
+  while (ntp < ntask) ntp <<= 1;
+  const int t = threadIdx.x, task = t % ntp, s = t / ntp, nseg = kRT / ntp;
   const int k0 = (int)((int64_t)s * K / nseg), k1 = (int)((int64_t)(s + 1) * K / nseg);
-  float acc[RP][4];
+  float acc[4][4];
 #pragma unroll
-  for (int a = 0; a < RP; ++a)
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
-  if (g < ng) {
-    const float* zb = g < gx ? X + 4 * g : Ys + 4 * (g - gx);
-    const int ldz = g < gx ? ldx : RP;
+    for (int c = 0; c < 4; ++c) acc[u][c] = 0.f;
+  if (task < ntask) {
+    const int a4 = task / gx, g = task - a4 * gx;
+    const float* yb = Ys + 4 * a4;
+    const float* xb = X + 4 * g;
     for (int q = k0; q < k1; ++q) {
-      const float4 z = *reinterpret_cast<const float4*>(zb + q * ldz);
-      const float* yr = Ys + q * RP;
+      const float4 y = *reinterpret_cast<const float4*>(yb + q * RP);
+      const float4 z = *reinterpret_cast<const float4*>(xb + q * ldx);
+      const float yv[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
-      for (int a4 = 0; a4 < GY; ++a4) {
-        const float4 y = *reinterpret_cast<const float4*>(yr + 4 * a4);
-        const float yv[4] = {y.x, y.y, y.z, y.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          acc[4 * a4 + u][0] = fmaf(yv[u], z.x, acc[4 * a4 + u][0]);
-          acc[4 * a4 + u][1] = fmaf(yv[u], z.y, acc[4 * a4 + u][1]);
-          acc[4 * a4 + u][2] = fmaf(yv[u], z.z, acc[4 * a4 + u][2]);
-          acc[4 * a4 + u][3] = fmaf(yv[u], z.w, acc[4 * a4 + u][3]);
-        }
+      for (int u = 0; u < 4; ++u) {
+        acc[u][0] = fmaf(yv[u], z.x, acc[u][0]);
+        acc[u][1] = fmaf(yv[u], z.y, acc[u][1]);
+        acc[u][2] = fmaf(yv[u], z.z, acc[u][2]);
+        acc[u][3] = fmaf(yv[u], z.w, acc[u][3]);
       }
     }
   }
-  for (int d = ngp; d < 32; d <<= 1)
+  for (int d = ntp; d < 32; d <<= 1)
 #pragma unroll
-    for (int a = 0; a < RP; ++a)
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][c] += __shfl_xor_sync(0xffffffffu, acc[a][c], d);
+      for (int c = 0; c < 4; ++c) acc[u][c] += __shfl_xor_sync(0xffffffffu, acc[u][c], d);
   const int lane = t & 31, warp = t >> 5;
-  if (lane < ngp && g < ng) {
+  if (lane < ntp && task < ntask) {
 #pragma unroll
-    for (int a = 0; a < RP; ++a)
-      *reinterpret_cast<float4*>(&Red[((warp * kMaxGroups + g) * RP + a) * 4]) =
-          make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+    for (int u = 0; u < 4; ++u)
+      *reinterpret_cast<float4*>(&Red[((warp * kMaxTasks + task) * 4 + u) * 4]) =
+          make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
   }
   __syncthreads();
-  for (int o = t; o < ng * RP * 4; o += kRT) {
-    const int gg = o / (RP * 4), rem = o - gg * (RP * 4);
-    float sum = Red[gg * RP * 4 + rem];
-    for (int w = 1; w < kRW; ++w) sum += Red[(w * kMaxGroups + gg) * RP * 4 + rem];
-    C[o] = sum;
+  for (int o = t; o < ntask * 16; o += kRT) {
+    const int tk = o >> 4, e = o & 15;
+    float sum = Red[tk * 16 + e];
+    for (int w = 1; w < kRW; ++w) sum += Red[(w * kMaxTasks + tk) * 16 + e];
+    const int a4 = tk / gx, g = tk - a4 * gx;
+    NUM[(4 * a4 + (e >> 2)) * ldn + 4 * g + (e & 3)] = sum;
   }
   __syncthreads();
+}
+
+// Upper-triangle entry e of an r x r matrix (row-major over k <= l).
+__device__ __forceinline__ void tri_index(int e, int r, int& k, int& l) {
+  k = 0;
+  while (e >= r - k) { e -= r - k; ++k; }
+  l = k + e;
+}
+
+// The Gram of the other factor from the grid's partials gp[G][E], in block
+// order: thread t < E * nch sums the blocks of chunk t / E (chunks of
+// consecutive blocks, in order) into Sg; gram_finish adds the chunks in
+// order and fills GR (both triangles).
+__device__ __forceinline__ int gram_chunks(int E) {
+  const int c = kRT / E;
+  return c < 1 ? 1 : c;
+}
+__device__ void gram_partial_sums(const float* gp, int E, float* Sg) {
+  const int G = gridDim.x, nch = gram_chunks(E), t = threadIdx.x;
+  if (t < E * nch) {
+    const int e = t % E, c = t / E;
+    const int b0 = (int)((int64_t)c * G / nch), b1 = (int)((int64_t)(c + 1) * G / nch);
+    float sum = 0.f;
+    for (int b = b0; b < b1; ++b) sum += __ldcg(gp + (int64_t)b * E + e);
+    Sg[c * E + e] = sum;
+  }
+}
+template <int RP>
+__device__ void gram_finish(const float* Sg, int E, int r, float* GR) {
+  const int nch = gram_chunks(E), t = threadIdx.x;
+  if (t < E) {
+    float sum = Sg[t];
+    for (int c = 1; c < nch; ++c) sum += Sg[c * E + t];
+    int k, l;
+    tri_index(t, r, k, l);
+    GR[k * RP + l] = sum;
+    GR[l * RP + k] = sum;
+  }
+}
+
+// The partial Gram of a slice of new factor values F[m][k] (m < nm, row
+// stride ld), upper triangle, into gp[blockIdx.x][E]: sums over m in order.
+template <typename Fn>
+__device__ void gram_partial(Fn val, int nm, int r, int E, float* gp) {
+  for (int e = threadIdx.x; e < E; e += kRT) {
+    int k, l;
+    tri_index(e, r, k, l);
+    float sum = 0.f;
+    for (int m = 0; m < nm; ++m) sum = fmaf(val(m, k), val(m, l), sum);
+    gp[(int64_t)blockIdx.x * E + e] = sum;
+  }
 }
 
 __device__ __forceinline__ void cp_async16(float* dst, const float* src) {
@@ -186,7 +240,8 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // Step 1 of a half step: the other factor's padded copy ([K][RP], 16-byte
 // rows) into Ys by asynchronous 16-byte copies (all in flight at once, no
-// registers), the block's own old values into O.  The caller synchronises.
+// registers), the block's own old values into O.  The caller waits for the
+// copies (cp_async_wait_all) and synchronises.
 template <int RP, bool HU>
 __device__ void load_operands(const ResArgs& a, float* Ys, float* O, float* On, int g0,
                               int nm) {
@@ -202,7 +257,6 @@ __device__ void load_operands(const ResArgs& a, float* Ys, float* O, float* On, 
     O[e] = v;
     On[e] = 0.f;
   }
-  cp_async_wait_all();
 }
 
 // One half step of this block.  HU = true: the H update over the block's
@@ -219,20 +273,23 @@ __device__ void half_step(const ResArgs& a, float* sm, const ResSmem<RP>& L, int
   float* Ys = sm + L.ys;
   float* O = sm + L.o;
   float* On = sm + L.on;
-  float* C = sm + L.c;
-  load_operands<RP, HU>(a, Ys, O, On, g0, nm);
+  float* NUM = sm + L.num;
+  float* GR = sm + L.gr;
+  float* Sg = sm + L.sg;
+  load_operands<RP, HU>(a, Ys, O, On, g0, nm);   // copies still in flight
+  gram_partial_sums(HU ? a.gpW : a.gpH, a.E, Sg);
+  cp_async_wait_all();
   __syncthreads();
-  // 2. numerators and Gram
+  gram_finish<RP>(Sg, a.E, r, GR);
+  // numerators (their own barriers also order GR)
   const int gx = (nm + 3) / 4;
-  contract<RP>(X, ldx, gx, Ys, K, sm + L.red, C);
-  // 3. den = O G + eps, new = O * num / den
-  const float* Gc = C + gx * RP * 4;   // group gx + l/4, row a = k, column l % 4
+  contract_num<RP>(X, ldx, gx, Ys, K, sm + L.red, NUM, L.ldn);
+  // den = O G + eps, new = O * num / den
   for (int e = t; e < nm * r; e += kRT) {
     const int m = e / r, k = e - m * r;
     float den = 0.f;
-    for (int l = 0; l < r; ++l)
-      den = fmaf(O[m * RP + l], Gc[((l >> 2) * RP + k) * 4 + (l & 3)], den);
-    const float num = C[((m >> 2) * RP + k) * 4 + (m & 3)];
+    for (int l = 0; l < r; ++l) den = fmaf(O[m * RP + l], GR[l * RP + k], den);
+    const float num = NUM[k * L.ldn + m];
     const float v = div_rn(__fmul_rn(O[m * RP + k], num), __fadd_rn(den, a.eps));
     On[m * RP + k] = v;
     if (HU) {
@@ -243,8 +300,10 @@ __device__ void half_step(const ResArgs& a, float* sm, const ResSmem<RP>& L, int
       a.Wp[(int64_t)(g0 + m) * RP + k] = v;
     }
   }
-  if (!check) return;
   __syncthreads();
+  // the partial Gram of this block's new values, for the other half step
+  gram_partial([&](int m, int k) { return On[m * RP + k]; }, nm, r, a.E, HU ? a.gpH : a.gpW);
+  if (!check) return;
   // 4. this slice's part of ||V - W H||^2: entries (K index q, own index m)
   double acc = 0.0;
   const int tot = K * nm;
@@ -301,6 +360,12 @@ __global__ void __launch_bounds__(kRT, 1) k_resident(const ResArgs a) {
     for (int j = t; j < a.n; j += kRT)
       Xr[j * a.ldr + ii] = ii < nr ? __ldg(a.V + (int64_t)(i0 + ii) * a.n + j) : 0.f;
   for (int e = t; e < (a.p > a.n ? a.p : a.n) * RP; e += kRT) sm[L.ys + e] = 0.f;
+  for (int e = t; e < RP * RP; e += kRT) sm[L.gr + e] = 0.f;
+  // partial Grams of this block's rows of the starting W and columns of H
+  gram_partial([&](int m, int k) { return a.W[(int64_t)(i0 + m) * a.r + k]; }, nr, a.r, a.E,
+               a.gpW);
+  gram_partial([&](int m, int k) { return a.H[(int64_t)k * a.n + j0 + m]; }, nc, a.r, a.E,
+               a.gpH);
   // the padded copies of this block's slices of the starting factors
   for (int e = t; e < nr * RP; e += kRT) {
     const int m = e / RP, k = e - m * RP;
@@ -395,14 +460,14 @@ const void* kernel_for(int r) {
 bool resident_supported(int64_t p, int64_t n, int r, int sms, size_t smem_optin) {
   if (r < 1 || r > kResidentMaxRank || p < 1 || n < 1 || sms < 1) return false;
   if (p > (1 << 20) || n > (1 << 20)) return false;
-  // output groups of four columns: the own slice's plus the Gram's
+  // 4 x 4 numerator tiles of the larger own slice
   const int64_t mnm = std::max((n + sms - 1) / sms, (p + sms - 1) / sms);
-  if ((mnm + 3) / 4 + rpad4(r) / 4 > kMaxGroups) return false;
+  if ((mnm + 3) / 4 * (rpad4(r) / 4) > kMaxTasks) return false;
   return smem_for((int)p, (int)n, r, sms) + 1024 <= smem_optin;
 }
 
-size_t resident_workspace_floats(int64_t p, int64_t n, int r) {
-  return (size_t)(p + n) * rpad4(r);
+size_t resident_workspace_floats(int64_t p, int64_t n, int r, int sms) {
+  return (size_t)(p + n) * rpad4(r) + 2 * (size_t)sms * (size_t)(r * (r + 1) / 2);
 }
 
 cudaError_t launch_resident(const float* V, float* W, float* H, int64_t p, int64_t n, int r,
@@ -418,6 +483,9 @@ cudaError_t launch_resident(const float* V, float* W, float* H, int64_t p, int64
   a.H = H;
   a.Wp = work;
   a.Hp = work + (size_t)p * rpad4(r);
+  a.E = r * (r + 1) / 2;
+  a.gpW = a.Hp + (size_t)n * rpad4(r);
+  a.gpH = a.gpW + (size_t)G * a.E;
   a.p = (int)p;
   a.n = (int)n;
   a.r = r;
@@ -443,7 +511,7 @@ cudaError_t launch_resident(const float* V, float* W, float* H, int64_t p, int64
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRT, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-  e = cudaMemsetAsync(bar, 0, sizeof(unsigned long long), st);
+  e = cudaMemsetAsync(bar, 0, kResidentBarWords * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel(kern, dim3((unsigned)G), dim3(kRT), args, smem, st);

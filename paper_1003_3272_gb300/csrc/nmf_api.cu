@@ -796,9 +796,10 @@ nmf_status nmf_converge_resident(nmf_ctx* c, int max_iters, double tol, int chec
   nmf_status s = NMF_OK;
   if (!c->res_work) {
     if ((s = dalloc(c, (void**)&c->res_work,
-                    resident_workspace_floats(c->p, c->n, c->r) * sizeof(float))) != NMF_OK ||
+                    resident_workspace_floats(c->p, c->n, c->r, c->sms) * sizeof(float))) != NMF_OK ||
         (s = dalloc(c, (void**)&c->res_fpart, sizeof(double) * (size_t)c->sms)) != NMF_OK ||
-        (s = dalloc(c, (void**)&c->res_bar, sizeof(unsigned long long))) != NMF_OK)
+        (s = dalloc(c, (void**)&c->res_bar,
+                    kResidentBarWords * sizeof(unsigned long long))) != NMF_OK)
       return s;
   }
   CK(launch_model_objective(c), "objective");
