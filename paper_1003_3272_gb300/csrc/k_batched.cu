@@ -41,7 +41,8 @@ namespace nmf {
 namespace {
 
 constexpr int kBR = 32;            // rank capacity (RPAD max)
-constexpr int kThreads = 192;      // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kThreads = 320;      // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int kEpi = kThreads - 64;  // epilogue threads: two warps per TMEM lane quarter
 constexpr int kBM = 128;
 constexpr uint64_t kWaitCycles = 3000ull * 1000 * 1000;
 constexpr int kSmemMax = 227 * 1024;
@@ -93,14 +94,15 @@ struct BShape {
   static constexpr int SMEM = STAGES * STAGE + GS + VS + 1024;
 };
 
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+static_assert(kEpi == 256, "epi_sync counts the epilogue threads");
 // epi_sync that also returns, to every epilogue thread alike, whether any of
 // them passed `flag` true (so that all of them leave a loop together).
 __device__ __forceinline__ bool epi_sync_or(bool flag) {
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      "bar.red.or.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
       : "=r"(r) : "r"((uint32_t)flag) : "memory");
   return r != 0;
 }
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(const BatchParams a)
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(ptx::smem_u32(&accf[b]), 1);
-      ptx::mbar_init(ptx::smem_u32(&acce[b]), 128);
+      ptx::mbar_init(ptx::smem_u32(&acce[b]), kEpi);
     }
     ptx::mbar_init(ptx::smem_u32(&done_bar), 1);
     s_abort = 0;
@@ -253,15 +255,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(const BatchParams a)
     }
     ptx::mma_commit(ptx::smem_u32(&done_bar));
   } else if (warp >= 2) {
-    // ---------------- epilogue warps (128 threads) ----------------
+    // ---------------- epilogue warps (256 threads) ----------------
+    // Two warps per tensor-memory lane quarter (warps w and w + 4): each
+    // thread owns one row of the item and one half of the ranks (kh).
     // Per item: the instance's Gram G and the row's old factor values are
-    // read, and den = old . G + eps formed, while the item is still being
-    // streamed; only the quotient old * num / den waits for the accumulator.
-    // den accumulates all ranks k at once (32 independent chains, G read as
-    // broadcast float4 rows), in the same order over l as a plain dot product.
+    // read, and den = old . G + eps formed for the thread's ranks while the
+    // item is still being streamed; only the quotient old * num / den waits
+    // for the accumulator.  den accumulates its ranks at once (16
+    // independent chains, G read as broadcast float4 rows), in the same
+    // order over l as a plain dot product.
     const int et = threadIdx.x - 64;
     const int quarter = warp & 3;                 // TMEM lanes 32 * (warp % 4)
     const int row = quarter * 32 + lane;
+    const int kh = (warp - 2) >> 2;               // ranks [16 kh, 16 kh + 16)
+    constexpr int KH = kBR / 2;
     ptx::pdl_wait();                              // the Gram launch has completed
     for (int i = i0; i < i1; ++i) {
       const int buf = (i - i0) & 1;
@@ -272,48 +279,48 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(const BatchParams a)
       const int64_t M = B.M[half];
       const int64_t m = (int64_t)it.y * kBM + row;
       const bool live = m < M;
+      const bool mine = KH * kh < r;              // this thread has ranks to update
       float* F = B.F[half];
       const int64_t ldf = B.ldf[half];
       epi_sync();                                 // Gs and Vs free (previous item done)
       {
-        float gv[kBR * kBR / 128];
+        float gv[kBR * kBR / kEpi];
 #pragma unroll
-        for (int j = 0; j < kBR * kBR / 128; ++j) gv[j] = __ldcg(B.Gpad[half] + et + 128 * j);
+        for (int j = 0; j < kBR * kBR / kEpi; ++j) gv[j] = __ldcg(B.Gpad[half] + et + kEpi * j);
 #pragma unroll
-        for (int j = 0; j < kBR * kBR / 128; ++j) Gs[et + 128 * j] = gv[j];
+        for (int j = 0; j < kBR * kBR / kEpi; ++j) Gs[et + kEpi * j] = gv[j];
       }
       float old[kBR];
 #pragma unroll
       for (int k = 0; k < kBR; ++k)
-        old[k] = (live && k < r) ? (half == 0 ? F[(int64_t)k * ldf + m] : F[m * ldf + k]) : 0.f;
+        old[k] = (live && mine && k < r) ? (half == 0 ? F[(int64_t)k * ldf + m] : F[m * ldf + k]) : 0.f;
       epi_sync();                                 // Gs complete
-      float den[kBR];
+      float den[KH];
 #pragma unroll
-      for (int k = 0; k < kBR; ++k) den[k] = 0.f;
+      for (int k = 0; k < KH; ++k) den[k] = 0.f;
+      if (mine) {
 #pragma unroll
-      for (int l = 0; l < kBR; ++l) {
-        if (l >= r) break;
-        const float4* gl = reinterpret_cast<const float4*>(Gs + l * kBR);
+        for (int l = 0; l < kBR; ++l) {
+          if (l >= r) break;
+          const float4* gl = reinterpret_cast<const float4*>(Gs + l * kBR + KH * kh);
 #pragma unroll
-        for (int q = 0; q < kBR / 4; ++q) {
-          const float4 g = gl[q];
-          den[4 * q + 0] = fmaf(old[l], g.x, den[4 * q + 0]);
-          den[4 * q + 1] = fmaf(old[l], g.y, den[4 * q + 1]);
-          den[4 * q + 2] = fmaf(old[l], g.z, den[4 * q + 2]);
-          den[4 * q + 3] = fmaf(old[l], g.w, den[4 * q + 3]);
+          for (int q = 0; q < KH / 4; ++q) {
+            const float4 g = gl[q];
+            den[4 * q + 0] = fmaf(old[l], g.x, den[4 * q + 0]);
+            den[4 * q + 1] = fmaf(old[l], g.y, den[4 * q + 1]);
+            den[4 * q + 2] = fmaf(old[l], g.z, den[4 * q + 2]);
+            den[4 * q + 3] = fmaf(old[l], g.w, den[4 * q + 3]);
+          }
         }
       }
       bool ok = ptx::mbar_wait(ptx::smem_u32(&accf[buf]), use & 1u, kWaitCycles);
       ok = __all_sync(0xffffffffu, ok);   // tensor-memory loads are warp-collective
       if (!ok) atomicExch(&s_abort, 1);
       ptx::tc_fence_after();
-      float num[kBR];
-      if (ok) {
-        ptx::tmem_ld16(tmem + (uint32_t)(buf * kBR) + ((uint32_t)(quarter * 32) << 16), num);
-        if (B.rpad > 16)
-          ptx::tmem_ld16(tmem + (uint32_t)(buf * kBR + 16) + ((uint32_t)(quarter * 32) << 16),
-                         num + 16);
-      }
+      float num[KH];
+      if (ok && KH * kh < B.rpad)
+        ptx::tmem_ld16(tmem + (uint32_t)(buf * kBR + KH * kh) + ((uint32_t)(quarter * 32) << 16),
+                       num);
       ptx::tc_fence_before();
       ptx::mbar_arrive(ptx::smem_u32(&acce[buf]));
       // an expired wait anywhere stops every epilogue thread alike
@@ -322,44 +329,49 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(const BatchParams a)
       // stores: H's columns and both planes directly (consecutive rows m are
       // consecutive addresses), W's rows through Vs below (the item's rows of
       // the row-major W are one contiguous block).
-      float v[kBR];
+      float v[KH];
 #pragma unroll
-      for (int k = 0; k < kBR; ++k) v[k] = 0.f;
-      if (live) {
+      for (int k = 0; k < KH; ++k) v[k] = 0.f;
+      if (live && mine) {
 #pragma unroll
-        for (int k0 = 0; k0 < kBR; k0 += 8) {
-          if (k0 >= r) break;
+        for (int k0 = 0; k0 < KH; k0 += 8) {
+          if (KH * kh + k0 >= r) break;
 #pragma unroll
           for (int k = k0; k < k0 + 8; ++k) {
-            const bool in = k < r;
-            v[k] = div_rn(in ? __fmul_rn(old[k], num[k]) : 0.f, in ? __fadd_rn(den[k], B.eps) : 1.f);
+            const int kk = KH * kh + k;
+            const bool in = kk < r;
+            const float o = kh ? old[KH + k] : old[k];   // static indices: old stays in registers
+            v[k] = div_rn(in ? __fmul_rn(o, num[k]) : 0.f, in ? __fadd_rn(den[k], B.eps) : 1.f);
           }
         }
 #pragma unroll
-        for (int k = 0; k < kBR; ++k) {
-          if (k >= r) break;
-          if (half == 0) F[(int64_t)k * ldf + m] = v[k];
-          plane_store(B.plane, B.op_hi[half], B.op_lo[half], (int64_t)k * B.ldop[half] + m, v[k]);
+        for (int k = 0; k < KH; ++k) {
+          const int kk = KH * kh + k;
+          if (kk >= r) break;
+          if (half == 0) F[(int64_t)kk * ldf + m] = v[k];
+          plane_store(B.plane, B.op_hi[half], B.op_lo[half], (int64_t)kk * B.ldop[half] + m, v[k]);
         }
       }
-      float* vrow = Vs + row * Sh::VLD;
+      float* vrow = Vs + row * Sh::VLD + KH * kh;
 #pragma unroll
-      for (int k = 0; k < kBR; k += 4)
+      for (int k = 0; k < KH; k += 4)
         *reinterpret_cast<float4*>(vrow + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
-      // Gram of the item's new rows (float32 over its 128 rows): two groups of
-      // 64 threads take 64 rows each, one 4 x 4 block of the 32 x 32 per
-      // thread; group 1's sums go through Gs (free until the next item),
-      // group 0 adds them and stores the float64 result in the item's slot.
+      // Gram of the item's new rows (float32 over its 128 rows), by warps
+      // 2-5: two groups of 64 threads take 64 rows each, one 4 x 4 block of
+      // the 32 x 32 per thread; group 1's sums go through Gs (free until the
+      // next item), group 0 adds them and stores the float64 result in the
+      // item's slot.
       epi_sync();
-      if (half == 1) {
-        // W's new rows m0 .. m0 + rows - 1 (row-major, ldf = r): one
-        // contiguous block, copied from Vs with consecutive threads on
-        // consecutive addresses
+      if (half == 1 && et >= 128) {
+        // (warps 6-9, while warps 2-5 form the Gram) W's new rows m0 ..
+        // m0 + rows - 1 (row-major, ldf = r): one contiguous block, copied
+        // from Vs with consecutive threads on consecutive addresses
+        const int e0 = et - 128;
         const int64_t m0 = (int64_t)it.y * kBM;
         const int total = (int)(M - m0 < kBM ? M - m0 : (int64_t)kBM) * r;
         const int dq = kBM / r, dr = kBM % r;
-        int rw = et / r, cl = et % r;
-        for (int e = et; e < total; e += kBM) {
+        int rw = e0 / r, cl = e0 % r;
+        for (int e = e0; e < total; e += 128) {
           F[(m0 + rw) * ldf + cl] = Vs[rw * Sh::VLD + cl];
           rw += dq;
           cl += dr;
@@ -373,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batched_tc(const BatchParams a)
         for (int x = 0; x < 4; ++x)
 #pragma unroll
           for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
-        if (bi * 4 < r && bj * 4 < r) {
+        if (et < 128 && bi * 4 < r && bj * 4 < r) {
 #pragma unroll 4
           for (int mm = 0; mm < 64; ++mm) {
             const float* vr = Vs + (grp * 64 + mm) * Sh::VLD;
