@@ -27,8 +27,6 @@
 //   6. a grid-wide barrier (a counter with bounded waits).
 // After each round every block sums the objective partials in block order,
 // so all blocks take the same stopping decision.
-#include <cooperative_groups.h>
-
 #include <algorithm>
 
 #include "nmf_internal.cuh"
@@ -217,8 +215,8 @@ __device__ void gram_finish(const float* Sg, int E, int r, float* GR) {
   }
 }
 
-// The partial Gram of a slice of new factor values F[m][k] (m < nm, row
-// stride ld), upper triangle, into gp[blockIdx.x][E]: sums over m in order.
+// The partial Gram of a slice of factor values val(m, k) (m < nm, k < r),
+// upper triangle, into gp[blockIdx.x][E]: float32 sums over m in order.
 template <typename Fn>
 __device__ void gram_partial(Fn val, int nm, int r, int E, float* gp) {
   for (int e = threadIdx.x; e < E; e += kRT) {
