@@ -332,6 +332,23 @@ def roofline(prec, p, n, r, res, clocks, workload="planted_8192x8192_r50"):
     return roof
 
 
+def pass_bounds(prec, p, n, r, value):
+    """The whole-step update rate against the two HBM bounds of an
+    iteration: V streamed twice (the H and the W update each read it once;
+    the bound of record) and V streamed once (an iteration that keeps column
+    panels of V in L2 between the two products).  Each bound is the measured
+    copy bandwidth over the algorithmic bytes of one or two streaming
+    launches; `value` includes everything else a step does, so each fraction
+    is a lower bound on the streams' own."""
+    pk = peaks()
+    bytes_l, _ = algorithmic(prec, p, n, r)
+    two = pk["hbm_gbs"] * 1e9 / (2.0 * bytes_l)
+    one = pk["hbm_gbs"] * 1e9 / bytes_l
+    return {"unit": "updates/s", "bytes_per_pass": int(bytes_l), "peak_gbs": pk["hbm_gbs"],
+            "two_pass": {"bound": round(two, 1), "frac": round(value / two, 4)},
+            "one_pass": {"bound": round(one, 1), "frac": round(value / one, 4)}}
+
+
 def batched_stored_objectives():
     """The float64 oracle's objectives after 100 iterations of sampled
     instances of the batched workload, from tests/golden/batched_objectives.json
@@ -875,6 +892,7 @@ def run_gpu(args, ws, rank, local):
                    "step": f"restart (operand copies + seeded W,H + Grams) + {iters} MM "
                            "iterations + objective + stopping test"},
         "roofline": roof, "e2e": e2e, "gpu_launches": main["launches"], "clocks": clocks,
+        "pass_bounds": pass_bounds(args.prec, p, n, r, main["value"]),
         "objective": main["objective"],
         "breakdown_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in kinds.items()},
     }

@@ -23,6 +23,18 @@ def test_algorithmic_figures_of_a_launch():
     assert b2 == 8192 * 8192 * 2 + 8192 * 50 * 2 + 8192 * 50 * 10 and f2 == f
 
 
+def test_pass_bounds(monkeypatch):
+    """Two-pass bound = copy bandwidth / (2 x one launch's bytes), one-pass
+    bound twice that, so the one-pass fraction is half the two-pass one."""
+    monkeypatch.setattr(bench, "peaks", lambda: {"hbm_gbs": 6000.0, "_source": "test"})
+    b, _ = bench.algorithmic("bf16x3", 8192, 8192, 50)
+    d = bench.pass_bounds("bf16x3", 8192, 8192, 50, 9000.0)
+    assert d["bytes_per_pass"] == b
+    assert abs(d["two_pass"]["bound"] - 6000e9 / (2 * b)) < 0.1
+    assert abs(d["one_pass"]["bound"] - 6000e9 / b) < 0.1
+    assert abs(d["one_pass"]["frac"] - d["two_pass"]["frac"] / 2) < 1e-4
+
+
 def test_traffic_only_while_the_kernel_sources_match(monkeypatch):
     key = "k_stream_tc/bf16x3/planted_8192x8192_r50"
     stored = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[key]
