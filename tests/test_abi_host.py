@@ -81,6 +81,8 @@ def test_device_loop_rejects_bad_arguments(lib):
     done, f = ctypes.c_int(), ctypes.c_double()
     assert lib.nmf_converge(None, 10, 1e-9, 1, ctypes.byref(done), ctypes.byref(f)) == nmf.EINVAL
     assert lib.nmf_run(None, 10, 1e-9, 1, ctypes.byref(done), ctypes.byref(f)) == nmf.EINVAL
+    assert lib.nmf_converge_resident(None, 10, 1e-9, 1, ctypes.byref(done),
+                                     ctypes.byref(f)) == nmf.EINVAL
 
 
 @pytest.mark.parametrize("bad", [
